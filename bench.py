@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark: bulk MTGP32 generation on GB300.
+
+Default workload (N = 1): 10 000 streams of one Mexp 11213 parameter set,
+output counts floor(2^U), U ~ Uniform[10, 22] (seed 7), about 5.04e9 uint32
+numbers (20 GB) per step.  A step is one replay of a recorded plan: a CUDA
+graph holding one persistent work-stealing launch over all streams.  Output
+(20 GB per step) is far larger than L2; in addition a 256 MiB buffer is
+rewritten between timed steps.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own
+instance of the workload (distinct stream seeds) on its own GPU; no data
+crosses ranks (weak scaling); the elapsed time is the max over ranks.
+
+--impl reference times the CPU oracle on the host cores instead (bounded
+samples of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1501_07701_gb300 import workloads  # noqa: E402
+
+METRIC = "Gnumbers/s and % of HBM-write roofline, bit-exact; serving p50/p99 latency"
+UNIT = "Gnumbers/s"
+KERNEL_SOURCES = ["paper_1501_07701_gb300/csrc/mtgp_fast.cuh",
+                  "paper_1501_07701_gb300/csrc/mtgp_kernels.cu"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fast_kernel_uneven_traffic.md")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not (m_b and m_h) or m_h.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+def workload(name: str, rank: int):
+    if name == "uneven":
+        w = workloads.uneven()
+        desc = ("uneven: 10000 MTGP32 Mexp 11213 streams, counts floor(2^U), U~U[10,22] "
+                "(seed 7)")
+    elif name == "equal":
+        w = workloads.equal()
+        desc = "equal: 4096 MTGP32 Mexp 11213 streams x 2^18"
+    elif name.startswith("long"):
+        w = workloads.long_streams(int(name[4:]))
+        desc = "long: 1024 MTGP32 Mexp %s streams x 2^20" % name[4:]
+    else:
+        raise SystemExit("unknown workload " + name)
+    n = w["seeds"].size
+    w["seeds"] = (w["seeds"].astype(np.uint64) + np.uint64(rank * n)).astype(np.uint32)
+    return w, desc
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 27, seed=0):
+    """Times the CPU oracle on a bounded random sample of the workload's
+    streams (outputs discarded batch by batch).  Returns (numbers/s, numbers,
+    seconds, streams)."""
+    import oracle
+    p = oracle.params_generate(w["mexp"], workloads.PARAM_SEED)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(w["seeds"].size)
+    # calibrate on a small batch
+    cal = order[:max(4, threads)]
+    cal_counts = np.minimum(w["counts"][cal], np.uint64(1 << 16))
+    st = np.stack([oracle.init_state(p, int(w["seeds"][i])) for i in cal])
+    t0 = time.perf_counter()
+    oracle.generate_many(p, st, np.arange(cal.size), cal_counts, 0, threads)
+    rate0 = float(cal_counts.sum()) / max(time.perf_counter() - t0, 1e-6)
+    target = rate0 * budget_s
+    picked, tot = [], 0
+    for i in order:
+        if tot >= target:
+            break
+        picked.append(int(i))
+        tot += int(w["counts"][i])
+    picked = np.array(picked)
+    states = np.stack([oracle.init_state(p, int(w["seeds"][i])) for i in picked])
+    counts = w["counts"][picked]
+    done, t_all = 0, 0.0
+    b0 = 0
+    while b0 < picked.size:
+        b1 = b0
+        acc = 0
+        while b1 < picked.size and (acc == 0 or acc + int(counts[b1]) <= max_batch):
+            acc += int(counts[b1])
+            b1 += 1
+        t0 = time.perf_counter()
+        oracle.generate_many(p, states[b0:b1], np.arange(b1 - b0), counts[b0:b1], 0, threads)
+        t_all += time.perf_counter() - t0
+        done += acc
+        b0 = b1
+    return done / t_all, done, t_all, picked.size
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    w, desc = workload(args.workload, 0)
+    # each step: a bounded sample sized so the whole run stays within ~2 minutes
+    per_step = min(10.0, max(0.05, 100.0 / max(1, args.steps + args.warmup)))
+    vals, secs, nums = [], [], []
+    for step in range(args.warmup + args.steps):
+        r, n, t, ns = oracle_rate(w, per_step, threads, seed=step)
+        if step >= args.warmup:
+            vals.append(r)
+            secs.append(t)
+            nums.append(n)
+    value = sum(nums) / sum(secs) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": desc, "format": "u32",
+                                        "sample": "random streams per step, ~%.2f s each" % per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d numbers over %d steps of random whole streams" % (
+                             sum(nums), len(nums))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1501_07701_gb300 import mtgp
+    from paper_1501_07701_gb300.build import build
+    build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w, desc = workload(args.workload, rank)
+    counts = w["counts"]
+    total = int(counts.sum())
+    stream = torch.cuda.Stream()
+    params = mtgp.mtgp_params_generate(w["mexp"], workloads.PARAM_SEED)
+    st = mtgp.mtgp_init_statuses(params, w["seeds"], stream)
+    out = torch.empty(total, dtype=torch.int32, device=dev)
+    ids = np.arange(w["seeds"].size, dtype=np.uint32)
+    plan = mtgp.mtgp_plan_create(st, ids, counts, mtgp.MTGP_U32, out)
+    tuned = None
+    if not args.no_autotune:
+        tuned = mtgp.mtgp_plan_autotune(plan)
+    info = mtgp.mtgp_plan_get_info(plan)
+
+    # bit-exact spot check of the first launch against the oracle (rank 0)
+    bit_exact = None
+    states0 = mtgp.mtgp_get_statuses(st, stream) if rank == 0 else None
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MiB > L2
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            mtgp.mtgp_plan_launch(plan, stream)
+            if _ == 0 and rank == 0:
+                stream.synchronize()
+                bit_exact = spot_check(w, counts, out, states0)
+            flush.fill_(1)
+    stream.synchronize()
+
+    # timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = cvd.split(",")[local_rank] if cvd else str(local_rank)
+    clocks = ClockSampler(smi_index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)   # let the sampler start
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            mtgp.mtgp_plan_launch(plan, stream)
+            ev[i][1].record(stream)
+            flush.fill_(i)
+    t1.record(stream)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    numbers_all = total * args.steps * world
+    value = numbers_all / elapsed / 1e9
+
+    # roofline of the dominant kernel (the persistent generation kernel)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    n_words = mtgp.mtgp_streams_info(st)[1]
+    alg_bytes = 4.0 * total + 8.0 * n_words * info["n_items"]
+    kern_avg = sum(kern_ms) / len(kern_ms) / 1e3
+    achieved = alg_bytes / kern_avg / 1e9
+
+    # self-measured write-only bandwidth (fill of the output buffer)
+    wb_a, wb_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        out.fill_(0)
+        wb_a.record(stream)
+        for _ in range(3):
+            out.fill_(7)
+        wb_b.record(stream)
+    stream.synchronize()
+    write_gbs = 3 * 4.0 * total / (wb_a.elapsed_time(wb_b) / 1e3) / 1e9
+
+    # end to end through the public API: host output buffer, copies inside
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(mtgp, torch, st, ids, counts, stream, args)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r, n, t, ns = oracle_rate(w, args.cpu_seconds, threads)
+        cpu = {"value": r / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d random whole streams of the workload, %d numbers, %.1f s" % (ns, n, t)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": desc, "numbers_per_step_per_gpu": total, "format": "u32",
+                       "parallelism": "independent streams per GPU" if world > 1 else "1 GPU",
+                       "l2": "20 GB written per step (> 129 MB L2) plus a 256 MiB rewrite "
+                             "between timed steps",
+                       "launch": info["config"], "grid_ctas": info["grid_ctas"],
+                       "autotuned": tuned is not None},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(),
+                         "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
+                         if peak_src == "measured" else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel_ms_avg": 1e3 * kern_avg, "kernel": "mtgp_fast_kernel"},
+            "write_only_fill_gbs": write_gbs,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": args.steps * info["kernel_launches"],
+            "bit_exact_sample": bit_exact,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def spot_check(w, counts, out, states0):
+    """Whole outputs of a few streams of the first launch vs the oracle."""
+    import oracle
+    p = oracle.params_generate(w["mexp"], workloads.PARAM_SEED)
+    offs = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
+    pick = [int(np.argmax(counts)), 0, counts.size - 1, counts.size // 2]
+    for s in pick:
+        ref, _ = oracle.generate(p, states0[s], int(counts[s]))
+        got = out[int(offs[s]):int(offs[s + 1])].cpu().numpy().view(np.uint32)
+        if not np.array_equal(ref, got):
+            return False
+    return True
+
+
+def measure_e2e(mtgp, torch, st, ids, counts, stream, args):
+    total = int(counts.sum())
+    try:
+        host = torch.empty(total, dtype=torch.int32, pin_memory=True)
+    except RuntimeError as e:
+        return {"value": None, "unit": UNIT, "error": "pinned host buffer: %s" % str(e)[:120]}
+    h2d = ids.nbytes + counts.nbytes
+    mtgp.mtgp_generate_to_host(st, ids, counts, mtgp.MTGP_U32, host, 0, stream)   # warm-up
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        mtgp.mtgp_generate_to_host(st, ids, counts, mtgp.MTGP_U32, host, 0, stream)
+    dt = time.perf_counter() - t0
+    return {"value": total * args.e2e_steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4 * total,
+            "steps": args.e2e_steps, "api": "mtgp_generate_to_host (pinned host output)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uneven")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus:
+        raise SystemExit("--gpus %d but WORLD_SIZE %d: launch N > 1 with torchrun" % (args.gpus, world))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * mtgp.h -- C ABI of libmtgp, bulk MTGP32 generation on GB300 (sm_103a).
+ *
+ * The library generates numbers from many independently initialised MTGP32
+ * streams that share one parameter set, the setting studied by
+ * Passerat-Palmbach, Mazel, Mahul and Hill, "Reliable Initialization of
+ * GPU-enabled Parallel Stochastic Simulations Using Mersenne Twister for
+ * Graphics Processors" (ESM 2010):
+ *   - a generator is a "parameterized status" (its signature) plus a "seed
+ *     status" chosen by the user (Sec. 3.1);
+ *   - each stream (one per block of threads in the paper, Sec. 2 and
+ *     Sec. 3.2) owns its state, which persists in global memory between
+ *     launches and lives in shared memory while it is being advanced (Sec. 2);
+ *   - the same sequence can be produced on a CPU (Sec. 3.2).
+ *
+ * Generator (the readings used where the paper prints no formula):
+ *   state x_0..x_{N-1}, N = floor(Mexp/32) + 1, mask keeps the high 32 - r
+ *   bits, r = 32N - Mexp;  for i = 0, 1, ...:
+ *     y = (x_i & mask) ^ x_{i+1};  y ^= y << sh1;  y ^= x_{i+pos} >> sh2;
+ *     x_{i+N} = y ^ REC[y & 15];
+ *     t = x_{i+pos-1};  t ^= t >> 16;  t ^= t >> 8;
+ *     o_i = x_{i+N} ^ TMP[t & 15];
+ *   float32 [1,2) = bits 0x3F800000 | (o_i >> 9);  float32 [0,1) = that - 1.
+ *   REC and TMP are GF(2)-linear 16-entry tables (XOR spans of 4 words).
+ *
+ * Conventions for every call:
+ *   - Every function returns an mtgp_status.  On any failure nothing is
+ *     written to caller buffers and stream states are unchanged; the reason
+ *     is available from mtgp_last_error() on the calling thread.
+ *   - No C++ exception crosses this boundary.
+ *   - Handles are thread-compatible: concurrent calls on distinct handles are
+ *     safe; concurrent calls on one handle must be serialised by the caller.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take it are asynchronous on that stream unless
+ *     stated otherwise.
+ *   - "device pointer" means memory allocated on the current CUDA device;
+ *     "host pointer" means ordinary (or pinned) host memory.
+ */
+#ifndef MTGP_H
+#define MTGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mtgp_params*  mtgp_params_t;   /* immutable after creation      */
+typedef struct mtgp_streams* mtgp_streams_t;  /* n_streams device-resident states */
+typedef struct mtgp_plan*    mtgp_plan_t;     /* a recorded batched launch     */
+
+typedef enum {
+    MTGP_OK = 0,
+    MTGP_EINVAL = 1,    /* an argument or a parameter field is out of range  */
+    MTGP_ENOMEM = 2,    /* host or device allocation failed                   */
+    MTGP_ECUDA = 3,     /* a CUDA runtime call failed                         */
+    MTGP_ETIMEOUT = 4,  /* a bounded wait ran out                             */
+    MTGP_EBUSY = 5,     /* admission refused: capacity is in use              */
+    MTGP_EIO = 6,       /* a file could not be read or parsed                 */
+    MTGP_EDEVICE = 7    /* a kernel reported an inconsistency (error word)    */
+} mtgp_status;
+
+typedef enum {
+    MTGP_U32 = 0,       /* uint32 words                                        */
+    MTGP_F32_12 = 1,    /* float32 in [1,2): exponent/mantissa bit-fill        */
+    MTGP_F32_01 = 2     /* float32 in [0,1): the [1,2) value minus 1 (exact)   */
+} mtgp_format;
+
+/* Field-by-field description of a parameterized status (Sec. 3.1).  The
+ * 16-entry tables are the "fast status" form (precomputed entries).        */
+typedef struct {
+    uint32_t mexp;          /* Mersenne exponent                               */
+    uint32_t n;             /* state words N; 0 = floor(mexp/32) + 1           */
+    uint32_t pos;           /* 1 <= pos <= N-1                                 */
+    uint32_t sh1, sh2;      /* 0..31                                           */
+    uint32_t mask;          /* 0 = 0xFFFFFFFF << (32N - mexp), needs 1..31     */
+    uint32_t rec_tbl[16];   /* recursion table, must be GF(2)-linear           */
+    uint32_t tmp_tbl[16];   /* tempering table, must be GF(2)-linear           */
+} mtgp_params_desc;
+
+/* ---------------------------------------------------------------------- */
+/* Parameterized status                                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Sec. 3.1 (parameterized status).  Reads a text file of `key value...`
+ * lines ('#' comments): mexp, pos, sh1, sh2, optional n and mask, and either
+ * rec_basis (4 words) or rec_tbl (16 words), likewise tmp_basis / tmp_tbl.
+ * Numbers are decimal or 0x-hex.  *out receives a new handle owned by the
+ * caller (free with mtgp_params_free).  MTGP_EIO if the file cannot be read
+ * or parsed, MTGP_EINVAL if a field is out of range or a table is not
+ * GF(2)-linear. */
+mtgp_status mtgp_params_load(const char* path, mtgp_params_t* out);
+
+/* Sec. 3.1 / Sec. 6 (the paper's parameter sets are not printed): draws a
+ * parameter set for `mexp` from a SplitMix64 stream seeded with `seed`, in
+ * the order sh1, sh2, pos, rec_basis[0..3], tmp_basis[0..3]
+ * (sh = 1 + d % 31; pos in [2, N - Wmin], Wmin = min(256, largest power of
+ * two <= N-2); basis words = d >> 32).  MTGP_EINVAL if mexp is a multiple of
+ * 32 or below 33. */
+mtgp_status mtgp_params_generate(uint32_t mexp, uint64_t seed, mtgp_params_t* out);
+
+/* Sec. 3.1: parameter set from explicit fields (`desc` is copied). */
+mtgp_status mtgp_params_create(const mtgp_params_desc* desc, mtgp_params_t* out);
+
+/* Copies the completed fields (n, mask, tables filled in) into *desc. */
+mtgp_status mtgp_params_get(mtgp_params_t params, mtgp_params_desc* desc);
+
+mtgp_status mtgp_params_free(mtgp_params_t params);
+
+/* ---------------------------------------------------------------------- */
+/* Streams: seed statuses and device-resident states                      */
+/* ---------------------------------------------------------------------- */
+
+/* Sec. 3.1 / Sec. 5.1 (seed status; one status per block, Sec. 3.2).
+ * Creates n_streams states on the current device, stream s initialised from
+ * the host array seeds[s] by w_0 = seed, w_i = 1812433253*(w_{i-1} ^
+ * (w_{i-1} >> 30)) + i.  `seeds` is a host pointer to n_streams words, read
+ * before the call returns.  The params handle is copied (the caller may free
+ * it).  Asynchronous on cuda_stream.  *out is owned by the caller. */
+mtgp_status mtgp_init_statuses(mtgp_params_t params, const uint32_t* seeds, uint32_t n_streams,
+                               void* cuda_stream, mtgp_streams_t* out);
+
+/* Overwrites all states from the host array `states` (n_streams x N words,
+ * row s = stream s, oldest word first).  Synchronous. */
+mtgp_status mtgp_set_statuses(mtgp_streams_t streams, const uint32_t* states, void* cuda_stream);
+
+/* Copies all states to the host array `states` (n_streams x N words, oldest
+ * word first: after c outputs of a stream its row is x_c .. x_{c+N-1}).
+ * Waits for cuda_stream.  Together with mtgp_set_statuses this is the
+ * checkpoint/restore pair. */
+mtgp_status mtgp_get_statuses(mtgp_streams_t streams, uint32_t* states, void* cuda_stream);
+
+/* Number of streams and words per state. */
+mtgp_status mtgp_streams_info(mtgp_streams_t streams, uint32_t* n_streams, uint32_t* n_words);
+
+/* Sec. 2 (per-block generator) and Sec. 3.2 (many statuses in one launch).
+ * Request j draws counts[j] numbers from stream stream_ids[j] into
+ * out[off_j .. off_j + counts[j]), off = exclusive prefix sum of counts.
+ * stream_ids and counts are host arrays of n_req entries; `out` is a device
+ * pointer to at least sum(counts) 4-byte elements (caller-owned).  Requests
+ * naming the same stream are applied in array order.  States advance in
+ * place.  Asynchronous on cuda_stream; host arrays are consumed before
+ * return.  MTGP_EINVAL for an id >= n_streams or a null pointer with a
+ * non-zero total. */
+mtgp_status mtgp_generate_u32(mtgp_streams_t streams, const uint32_t* stream_ids,
+                              const uint64_t* counts, uint32_t n_req, uint32_t* out,
+                              void* cuda_stream);
+
+/* As mtgp_generate_u32, with fmt MTGP_F32_12 or MTGP_F32_01 (MTGP_U32 is also
+ * accepted and writes the integer bit patterns). */
+mtgp_status mtgp_generate_f32(mtgp_streams_t streams, const uint32_t* stream_ids,
+                              const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
+                              float* out, void* cuda_stream);
+
+/* Sec. 3.2 (the same streams feeding CPU code): as mtgp_generate_u32/_f32 but
+ * `host_out` is a host pointer (pinned memory gives full copy bandwidth).
+ * Generation runs in chunks of at most `chunk_bytes` (0 = 1 GiB) into a
+ * library-owned device staging area, overlapped with device-to-host copies.
+ * Returns after all numbers are in host_out (synchronous). */
+mtgp_status mtgp_generate_to_host(mtgp_streams_t streams, const uint32_t* stream_ids,
+                                  const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
+                                  void* host_out, uint64_t chunk_bytes, void* cuda_stream);
+
+/* Waits for cuda_stream and reads the device error word of this handle.
+ * MTGP_EDEVICE if a kernel recorded an inconsistency since the last check
+ * (the word is then cleared). */
+mtgp_status mtgp_check(mtgp_streams_t streams, void* cuda_stream);
+
+mtgp_status mtgp_streams_free(mtgp_streams_t streams);
+
+/* ---------------------------------------------------------------------- */
+/* Launch configuration and autotuning                                    */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    uint32_t warps_per_cta;   /* block size / 32: 1..16                         */
+    uint32_t ctas_per_sm;     /* resident CTAs per SM (0 = occupancy maximum)   */
+    uint32_t words_per_lane;  /* sub-steps per parallel step (4 or 8); the
+                                 window is 32 * words_per_lane <= N - pos      */
+    uint32_t kernel;          /* 0 = register-resident path when available,
+                                 1 = shared-memory ring path (any parameters)  */
+} mtgp_launch_config;
+
+mtgp_status mtgp_get_launch_config(mtgp_streams_t streams, mtgp_launch_config* cfg);
+mtgp_status mtgp_set_launch_config(mtgp_streams_t streams, const mtgp_launch_config* cfg);
+
+/* Times candidate configurations on a scratch copy of up to `sample_streams`
+ * states (the handle's states are not advanced), `sample_count` numbers per
+ * stream, in format `fmt`; installs and returns the fastest.  Results are
+ * cached per process by (device, N, format).  Synchronous. */
+mtgp_status mtgp_autotune(mtgp_streams_t streams, mtgp_format fmt, uint32_t sample_streams,
+                          uint64_t sample_count, mtgp_launch_config* best);
+
+/* ---------------------------------------------------------------------- */
+/* Plans: one persistent launch replayed from a CUDA graph                */
+/* ---------------------------------------------------------------------- */
+
+/* Records a batched launch for the requests (same meaning as
+ * mtgp_generate_u32; every request in format `fmt`; `out` is a device
+ * pointer that must stay valid while the plan is used).  The work table is
+ * sorted longest stream first and uploaded once; launching replays a CUDA
+ * graph (reset of the work counter + one persistent kernel whose warps claim
+ * streams from that table).  The plan keeps a reference to `streams`. */
+mtgp_status mtgp_plan_create(mtgp_streams_t streams, const uint32_t* stream_ids,
+                             const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
+                             void* out, mtgp_plan_t* plan);
+
+/* Replays the plan on cuda_stream: every launch draws the next counts[j]
+ * numbers of each stream (states advance). */
+mtgp_status mtgp_plan_launch(mtgp_plan_t plan, void* cuda_stream);
+
+typedef struct {
+    uint64_t total_numbers;   /* sum of counts                                 */
+    uint32_t n_items;         /* distinct streams in the plan                  */
+    uint32_t kernel_launches; /* kernels per plan launch                       */
+    mtgp_launch_config config;
+    uint32_t grid_ctas;
+} mtgp_plan_info;
+
+/* Times the tuning candidates on this plan's own work table, on a scratch
+ * copy of all states (the handle's states are not advanced; the plan's `out`
+ * buffer is overwritten), installs the fastest in the plan and re-records its
+ * graph.  Synchronous. */
+mtgp_status mtgp_plan_autotune(mtgp_plan_t plan, mtgp_launch_config* best);
+
+mtgp_status mtgp_plan_get_info(mtgp_plan_t plan, mtgp_plan_info* info);
+mtgp_status mtgp_plan_free(mtgp_plan_t plan);
+
+/* ---------------------------------------------------------------------- */
+
+/* Message for the last failure on the calling thread ("" if none). */
+const char* mtgp_last_error(void);
+
+/* Library version string. */
+const char* mtgp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTGP_H */

@@ -75,8 +75,12 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            # MTGP_ORACLE_LIB loads a prebuilt variant instead (used by the
+            # mutation test to check that the pins reject planted mistakes).
+            path = os.environ.get("MTGP_ORACLE_LIB")
+            if not path:
+                path = build()
+            lib = ctypes.CDLL(path)
             P = ctypes.POINTER(Params)
             u32p = ctypes.POINTER(ctypes.c_uint32)
             u64p = ctypes.POINTER(ctypes.c_uint64)

@@ -1,0 +1,1192 @@
+// C ABI of libmtgp: parameter sets, device-resident stream states, batched
+// generation (direct calls, recorded plans replayed from CUDA graphs, and a
+// chunked device-to-host path), launch configuration and autotuning.
+#include "mtgp_runtime.h"
+
+#include <algorithm>
+#include <cerrno>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using namespace mtgp;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+mtgp_status mtgp::fail(mtgp_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+mtgp_status mtgp::fail_cuda(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? MTGP_ENOMEM : MTGP_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+mtgp_status mtgp::ok()
+{
+    g_last_error.clear();
+    return MTGP_OK;
+}
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                                      \
+    }                                                                                  \
+    catch (const std::bad_alloc&) { return fail(MTGP_ENOMEM, "host allocation failed"); } \
+    catch (...) { return fail(MTGP_EINVAL, "unexpected internal error"); }
+
+#define CUDA_TRY(call, what)                   \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess)                 \
+            return fail_cuda(e_, what);        \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Parameter sets (Sec. 3.1: the parameterized status; "fast" statuses carry
+// precomputed tables)
+// ---------------------------------------------------------------------------
+static bool table_is_linear(const uint32_t t[16])
+{
+    if (t[0] != 0)
+        return false;
+    for (int a = 0; a < 16; ++a)
+        for (int b = 0; b < 16; ++b)
+            if (t[a ^ b] != (t[a] ^ t[b]))
+                return false;
+    return true;
+}
+
+static void span(const uint32_t basis[4], uint32_t t[16])
+{
+    for (int k = 0; k < 16; ++k) {
+        uint32_t v = 0;
+        for (int b = 0; b < 4; ++b)
+            if ((k >> b) & 1)
+                v ^= basis[b];
+        t[k] = v;
+    }
+}
+
+static mtgp_status complete_desc(mtgp_params_desc& d)
+{
+    if (d.n == 0)
+        d.n = d.mexp / 32u + 1u;
+    if (d.mask == 0) {
+        const long long r = 32LL * d.n - (long long)d.mexp;
+        if (r < 1 || r > 31)
+            return fail(MTGP_EINVAL, "mask: 32N - Mexp = %lld is not in 1..31 (give mask explicitly)", r);
+        d.mask = 0xFFFFFFFFu << (uint32_t)r;
+    }
+    if (d.n < 2 || d.n > MTGP_MAX_N)
+        return fail(MTGP_EINVAL, "N = %u out of range 2..%u", d.n, (unsigned)MTGP_MAX_N);
+    if (d.pos < 1 || d.pos > d.n - 1)
+        return fail(MTGP_EINVAL, "pos = %u out of range 1..N-1 (N = %u)", d.pos, d.n);
+    if (d.sh1 > 31 || d.sh2 > 31)
+        return fail(MTGP_EINVAL, "shift out of range 0..31 (sh1 = %u, sh2 = %u)", d.sh1, d.sh2);
+    if (!table_is_linear(d.rec_tbl))
+        return fail(MTGP_EINVAL, "recursion table is not GF(2)-linear");
+    if (!table_is_linear(d.tmp_tbl))
+        return fail(MTGP_EINVAL, "tempering table is not GF(2)-linear");
+    return MTGP_OK;
+}
+
+static void to_kparams(const mtgp_params_desc& d, KParams& k)
+{
+    k.n = d.n;
+    k.np = (d.n + 3u) & ~3u;
+    k.pos = d.pos;
+    k.sh1 = d.sh1;
+    k.sh2 = d.sh2;
+    k.mask = d.mask;
+    for (int i = 0; i < 16; ++i) {
+        k.rec[i] = d.rec_tbl[i];
+        k.tmp[i] = d.tmp_tbl[i];
+        k.flt[i] = (d.tmp_tbl[i] >> 9) | 0x3F800000u;
+    }
+}
+
+static mtgp_status make_params(const mtgp_params_desc& in, mtgp_params_t* out)
+{
+    if (!out)
+        return fail(MTGP_EINVAL, "null output handle");
+    mtgp_params_desc d = in;
+    mtgp_status st = complete_desc(d);
+    if (st != MTGP_OK)
+        return st;
+    mtgp_params* p = new mtgp_params;
+    p->d = d;
+    to_kparams(d, p->k);
+    *out = p;
+    return ok();
+}
+
+extern "C" mtgp_status mtgp_params_create(const mtgp_params_desc* desc, mtgp_params_t* out)
+{
+    GUARD_BEGIN
+    if (!desc)
+        return fail(MTGP_EINVAL, "null desc");
+    return make_params(*desc, out);
+    GUARD_END
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): golden-ratio increment, then two
+// xor-shift-multiply rounds and a final xor-shift.
+static uint64_t sm64(uint64_t& s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+extern "C" mtgp_status mtgp_params_generate(uint32_t mexp, uint64_t seed, mtgp_params_t* out)
+{
+    GUARD_BEGIN
+    if (mexp < 33 || mexp % 32u == 0)
+        return fail(MTGP_EINVAL, "Mexp = %u unusable (needs >= 33 and not a multiple of 32)", mexp);
+    mtgp_params_desc d;
+    std::memset(&d, 0, sizeof d);
+    d.mexp = mexp;
+    d.n = mexp / 32u + 1u;
+    uint64_t s = seed;
+    d.sh1 = 1u + (uint32_t)(sm64(s) % 31u);
+    d.sh2 = 1u + (uint32_t)(sm64(s) % 31u);
+    const uint64_t dp = sm64(s);
+    uint32_t wmin = 1;
+    while (wmin * 2u <= d.n - 2u && wmin < 256u)
+        wmin *= 2u;
+    d.pos = 2u + (uint32_t)(dp % (uint64_t)(d.n - wmin - 1u));
+    uint32_t rb[4], tb[4];
+    for (int b = 0; b < 4; ++b)
+        rb[b] = (uint32_t)(sm64(s) >> 32);
+    for (int b = 0; b < 4; ++b)
+        tb[b] = (uint32_t)(sm64(s) >> 32);
+    span(rb, d.rec_tbl);
+    span(tb, d.tmp_tbl);
+    return make_params(d, out);
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_params_load(const char* path, mtgp_params_t* out)
+{
+    GUARD_BEGIN
+    if (!path)
+        return fail(MTGP_EINVAL, "null path");
+    std::ifstream f(path);
+    if (!f)
+        return fail(MTGP_EIO, "cannot open %s", path);
+    mtgp_params_desc d;
+    std::memset(&d, 0, sizeof d);
+    bool have_rec = false, have_tmp = false, have_mexp = false, have_pos = false, have_sh1 = false,
+         have_sh2 = false;
+    std::string line;
+    int lineno = 0;
+    while (std::getline(f, line)) {
+        ++lineno;
+        const size_t hash = line.find('#');
+        if (hash != std::string::npos)
+            line.resize(hash);
+        std::istringstream ls(line);
+        std::string key;
+        if (!(ls >> key))
+            continue;
+        std::vector<uint64_t> vals;
+        std::string tok;
+        while (ls >> tok) {
+            errno = 0;
+            char* end = nullptr;
+            const unsigned long long v = std::strtoull(tok.c_str(), &end, 0);
+            if (errno || !end || *end || v > 0xFFFFFFFFull)
+                return fail(MTGP_EIO, "%s:%d: bad number '%s'", path, lineno, tok.c_str());
+            vals.push_back(v);
+        }
+        auto one = [&](uint32_t& dst, bool* flag) -> bool {
+            if (vals.size() != 1)
+                return false;
+            dst = (uint32_t)vals[0];
+            if (flag)
+                *flag = true;
+            return true;
+        };
+        bool good = true;
+        if (key == "mexp")
+            good = one(d.mexp, &have_mexp);
+        else if (key == "n")
+            good = one(d.n, nullptr);
+        else if (key == "pos")
+            good = one(d.pos, &have_pos);
+        else if (key == "sh1")
+            good = one(d.sh1, &have_sh1);
+        else if (key == "sh2")
+            good = one(d.sh2, &have_sh2);
+        else if (key == "mask")
+            good = one(d.mask, nullptr);
+        else if (key == "rec_basis" || key == "tmp_basis") {
+            if (vals.size() != 4)
+                good = false;
+            else {
+                uint32_t b[4];
+                for (int i = 0; i < 4; ++i)
+                    b[i] = (uint32_t)vals[i];
+                span(b, key == "rec_basis" ? d.rec_tbl : d.tmp_tbl);
+                (key == "rec_basis" ? have_rec : have_tmp) = true;
+            }
+        } else if (key == "rec_tbl" || key == "tmp_tbl") {
+            if (vals.size() != 16)
+                good = false;
+            else {
+                uint32_t* t = key == "rec_tbl" ? d.rec_tbl : d.tmp_tbl;
+                for (int i = 0; i < 16; ++i)
+                    t[i] = (uint32_t)vals[i];
+                (key == "rec_tbl" ? have_rec : have_tmp) = true;
+            }
+        } else {
+            continue;   // unknown keys (e.g. state, outputs in test fixtures) are ignored
+        }
+        if (!good)
+            return fail(MTGP_EIO, "%s:%d: wrong number of values for '%s'", path, lineno, key.c_str());
+    }
+    if (!(have_mexp && have_pos && have_sh1 && have_sh2 && have_rec && have_tmp))
+        return fail(MTGP_EIO, "%s: missing field (need mexp, pos, sh1, sh2, rec_*, tmp_*)", path);
+    return make_params(d, out);
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_params_get(mtgp_params_t params, mtgp_params_desc* desc)
+{
+    if (!params || !desc)
+        return fail(MTGP_EINVAL, "null argument");
+    *desc = params->d;
+    return ok();
+}
+
+extern "C" mtgp_status mtgp_params_free(mtgp_params_t params)
+{
+    delete params;
+    return ok();
+}
+
+// ---------------------------------------------------------------------------
+// Work tables
+// ---------------------------------------------------------------------------
+mtgp_status mtgp::build_work(uint32_t n_streams, const uint32_t* ids, const uint64_t* counts,
+                             const int32_t* fmts, uint32_t fmt_all, uint32_t n_req,
+                             uint64_t out_base, Work& w)
+{
+    w.items.clear();
+    w.segs.clear();
+    w.total = 0;
+    w.max_item = 0;
+    if (n_req == 0)
+        return MTGP_OK;
+    if (!ids || !counts)
+        return fail(MTGP_EINVAL, "null request arrays");
+    std::vector<uint32_t> order;
+    order.reserve(n_req);
+    uint64_t total = 0;
+    for (uint32_t j = 0; j < n_req; ++j) {
+        if (ids[j] >= n_streams)
+            return fail(MTGP_EINVAL, "stream id %u >= n_streams %u (request %u)", ids[j], n_streams, j);
+        if (fmts && (fmts[j] < 0 || fmts[j] > 2))
+            return fail(MTGP_EINVAL, "format %d of request %u", fmts[j], j);
+        if (counts[j] > (1ull << 50) || total + counts[j] < total)
+            return fail(MTGP_EINVAL, "count too large (request %u)", j);
+        total += counts[j];
+        if (counts[j])
+            order.push_back(j);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return ids[a] < ids[b]; });
+    // exclusive scan of counts in request order gives the output offsets
+    std::vector<uint64_t> off(n_req);
+    uint64_t acc = out_base;
+    for (uint32_t j = 0; j < n_req; ++j) {
+        off[j] = acc;
+        acc += counts[j];
+    }
+    size_t i = 0;
+    while (i < order.size()) {
+        const uint32_t sid = ids[order[i]];
+        WorkItem it;
+        it.stream = sid;
+        it.seg_begin = (uint32_t)w.segs.size();
+        it.pad = 0;
+        uint64_t g = 0;
+        while (i < order.size() && ids[order[i]] == sid) {
+            const uint32_t j = order[i];
+            Segment s;
+            s.g_start = g;
+            s.count = counts[j];
+            s.out_off = off[j];
+            s.fmt = fmts ? (uint32_t)fmts[j] : fmt_all;
+            s.pad = 0;
+            w.segs.push_back(s);
+            g += counts[j];
+            ++i;
+        }
+        it.nseg = (uint32_t)w.segs.size() - it.seg_begin;
+        w.items.push_back(it);
+        w.max_item = std::max(w.max_item, g);
+    }
+    // Longest stream first: a warp that starts late only gets short streams.
+    std::vector<uint64_t> tot(w.items.size());
+    for (size_t k = 0; k < w.items.size(); ++k) {
+        const Segment& l = w.segs[w.items[k].seg_begin + w.items[k].nseg - 1];
+        tot[k] = l.g_start + l.count;
+    }
+    std::vector<uint32_t> idx(w.items.size());
+    for (size_t k = 0; k < idx.size(); ++k)
+        idx[k] = (uint32_t)k;
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return tot[a] > tot[b]; });
+    std::vector<WorkItem> sorted(w.items.size());
+    for (size_t k = 0; k < idx.size(); ++k)
+        sorted[k] = w.items[idx[k]];
+    w.items.swap(sorted);
+    w.total = total;
+    return MTGP_OK;
+}
+
+size_t mtgp::table_bytes(const Work& w, size_t* items_off, size_t* segs_off)
+{
+    const size_t a = 256;
+    const size_t io = a;
+    const size_t so = io + ((w.items.size() * sizeof(WorkItem) + a - 1) / a) * a;
+    if (items_off)
+        *items_off = io;
+    if (segs_off)
+        *segs_off = so;
+    return so + w.segs.size() * sizeof(Segment);
+}
+
+void mtgp::fill_table(const Work& w, void* host)
+{
+    size_t io, so;
+    table_bytes(w, &io, &so);
+    std::memset(host, 0, io);   // work counter (first word) = 0
+    if (!w.items.empty())
+        std::memcpy((char*)host + io, w.items.data(), w.items.size() * sizeof(WorkItem));
+    if (!w.segs.empty())
+        std::memcpy((char*)host + so, w.segs.data(), w.segs.size() * sizeof(Segment));
+}
+
+// ---------------------------------------------------------------------------
+// Streams
+// ---------------------------------------------------------------------------
+DeviceGuard::DeviceGuard(int dev)
+{
+    prev = -1;
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+        cudaSetDevice(dev);
+    else
+        prev = -1;
+}
+DeviceGuard::~DeviceGuard()
+{
+    if (prev >= 0)
+        cudaSetDevice(prev);
+}
+
+static void free_slot(TableSlot& s)
+{
+    if (s.ev_recorded)
+        cudaEventSynchronize(s.ev);
+    if (s.host)
+        cudaFreeHost(s.host);
+    if (s.dev)
+        cudaFree(s.dev);
+    s.host = nullptr;
+    s.dev = nullptr;
+    s.cap = 0;
+    s.ev_recorded = false;
+}
+
+static void destroy_streams(mtgp_streams* h)
+{
+    if (!h)
+        return;
+    DeviceGuard g(h->device);
+    for (auto& s : h->slots) {
+        free_slot(s);
+        if (s.ev)
+            cudaEventDestroy(s.ev);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (h->stage[b])
+            cudaFree(h->stage[b]);
+        if (h->ev_gen[b])
+            cudaEventDestroy(h->ev_gen[b]);
+        if (h->ev_copy[b])
+            cudaEventDestroy(h->ev_copy[b]);
+    }
+    if (h->copy_stream)
+        cudaStreamDestroy(h->copy_stream);
+    if (h->d_states)
+        cudaFree(h->d_states);
+    if (h->d_err)
+        cudaFree(h->d_err);
+    delete h;
+}
+
+extern "C" mtgp_status mtgp_init_statuses(mtgp_params_t params, const uint32_t* seeds,
+                                          uint32_t n_streams, void* cuda_stream, mtgp_streams_t* out)
+{
+    GUARD_BEGIN
+    if (!params || !out || (n_streams && !seeds))
+        return fail(MTGP_EINVAL, "null argument");
+    if (n_streams == 0)
+        return fail(MTGP_EINVAL, "n_streams must be >= 1");
+    mtgp_streams* h = new mtgp_streams;
+    h->P = *params;
+    h->n_streams = n_streams;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail_cuda(e, "cudaGetDevice");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    auto bail = [&](cudaError_t err, const char* what) {
+        mtgp_status st = fail_cuda(err, what);
+        destroy_streams(h);
+        return st;
+    };
+    const size_t bytes = (size_t)n_streams * h->P.k.np * sizeof(uint32_t);
+    if ((e = cudaMalloc(&h->d_states, bytes)) != cudaSuccess)
+        return bail(e, "cudaMalloc(states)");
+    if ((e = cudaMalloc(&h->d_err, sizeof(int))) != cudaSuccess)
+        return bail(e, "cudaMalloc(error word)");
+    if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), s)) != cudaSuccess)
+        return bail(e, "cudaMemsetAsync");
+    for (auto& sl : h->slots)
+        if ((e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e, "cudaEventCreate");
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaEventCreateWithFlags(&h->ev_gen[b], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_copy[b], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e, "cudaEventCreate");
+    }
+    if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "cudaStreamCreate");
+    // seeds -> device through a temporary buffer, then the init kernel
+    uint32_t* d_seeds = nullptr;
+    if ((e = cudaMallocAsync((void**)&d_seeds, (size_t)n_streams * 4, s)) != cudaSuccess)
+        return bail(e, "cudaMallocAsync(seeds)");
+    if ((e = cudaMemcpyAsync(d_seeds, seeds, (size_t)n_streams * 4, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess) {
+        cudaFreeAsync(d_seeds, s);
+        return bail(e, "cudaMemcpyAsync(seeds)");
+    }
+    e = launch_init(h->P.k, d_seeds, n_streams, h->d_states, s);
+    cudaFreeAsync(d_seeds, s);
+    if (e != cudaSuccess)
+        return bail(e, "init kernel launch");
+    // pageable seeds: the copy above is complete when cudaMemcpyAsync returns
+    h->cfg = default_config(h->P.k);
+    *out = h;
+    return ok();
+    GUARD_END
+}
+
+LaunchCfg mtgp::default_config(const KParams& P)
+{
+    LaunchCfg c;
+    c.warps_per_cta = 4;
+    c.ctas_per_sm = 0;
+    c.k = 8;
+    c.kernel = 0;
+    if (!fast_supported(P, 8))
+        c.k = fast_supported(P, 4) ? 4 : 8;
+    return c;
+}
+
+extern "C" mtgp_status mtgp_streams_info(mtgp_streams_t st, uint32_t* n_streams, uint32_t* n_words)
+{
+    if (!st)
+        return fail(MTGP_EINVAL, "null handle");
+    if (n_streams)
+        *n_streams = st->n_streams;
+    if (n_words)
+        *n_words = st->P.k.n;
+    return ok();
+}
+
+extern "C" mtgp_status mtgp_set_statuses(mtgp_streams_t st, const uint32_t* states, void* cuda_stream)
+{
+    GUARD_BEGIN
+    if (!st || !states)
+        return fail(MTGP_EINVAL, "null argument");
+    DeviceGuard g(st->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t n = st->P.k.n, np = st->P.k.np;
+    CUDA_TRY(cudaMemcpy2DAsync(st->d_states, np * 4, states, n * 4, n * 4, st->n_streams,
+                               cudaMemcpyHostToDevice, s),
+             "cudaMemcpy2DAsync(set statuses)");
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_get_statuses(mtgp_streams_t st, uint32_t* states, void* cuda_stream)
+{
+    GUARD_BEGIN
+    if (!st || !states)
+        return fail(MTGP_EINVAL, "null argument");
+    DeviceGuard g(st->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t n = st->P.k.n, np = st->P.k.np;
+    CUDA_TRY(cudaMemcpy2DAsync(states, n * 4, st->d_states, np * 4, n * 4, st->n_streams,
+                               cudaMemcpyDeviceToHost, s),
+             "cudaMemcpy2DAsync(get statuses)");
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return ok();
+    GUARD_END
+}
+
+// Resolves the geometry for the handle's configuration (cached).
+mtgp_status mtgp::geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t n_items, Geometry* g)
+{
+    const auto key = std::make_tuple(cfg.warps_per_cta, cfg.ctas_per_sm, cfg.k, cfg.kernel);
+    if (!(st->geo_valid && st->geo_key == key)) {
+        Geometry full;
+        cudaError_t e = plan_geometry(st->P.k, cfg, 0x7FFFFFFF, st->device, &full);
+        if (e != cudaSuccess)
+            return fail_cuda(e, "launch geometry");
+        st->geo_cap = full;
+        st->geo_key = key;
+        st->geo_valid = true;
+    }
+    *g = st->geo_cap;
+    const long long warps = g->threads / 32;
+    const long long want = ((long long)n_items + warps - 1) / warps;
+    g->grid = (int)std::max(1LL, std::min<long long>(want, st->geo_cap.grid));
+    return MTGP_OK;
+}
+
+// Uploads a work table through the handle's slot ring and launches.
+mtgp_status mtgp::launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
+                              cudaStream_t s)
+{
+    if (w.items.empty())
+        return MTGP_OK;
+    TableSlot& sl = st->slots[st->next_slot];
+    st->next_slot = (st->next_slot + 1) % (int)st->slots.size();
+    if (sl.ev_recorded) {
+        CUDA_TRY(cudaEventSynchronize(sl.ev), "cudaEventSynchronize(table slot)");
+        sl.ev_recorded = false;
+    }
+    size_t io, so;
+    const size_t bytes = table_bytes(w, &io, &so);
+    if (bytes > sl.cap) {
+        if (sl.host)
+            cudaFreeHost(sl.host);
+        if (sl.dev)
+            cudaFree(sl.dev);
+        sl.host = nullptr;
+        sl.dev = nullptr;
+        sl.cap = 0;
+        const size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
+        CUDA_TRY(cudaMallocHost(&sl.host, cap), "cudaMallocHost(work table)");
+        CUDA_TRY(cudaMalloc(&sl.dev, cap), "cudaMalloc(work table)");
+        sl.cap = cap;
+    }
+    fill_table(w, sl.host);
+    CUDA_TRY(cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, s),
+             "cudaMemcpyAsync(work table)");
+    Geometry g;
+    mtgp_status stt = geometry_for(st, cfg, (uint32_t)w.items.size(), &g);
+    if (stt != MTGP_OK)
+        return stt;
+    GenArgs a;
+    a.P = st->P.k;
+    a.states = st->d_states;
+    a.n_streams = st->n_streams;
+    a.items = (const WorkItem*)((char*)sl.dev + io);
+    a.segs = (const Segment*)((char*)sl.dev + so);
+    a.n_items = (uint32_t)w.items.size();
+    a.counter = (uint32_t*)sl.dev;
+    a.out = (uint32_t*)out;
+    a.err = st->d_err;
+    CUDA_TRY(launch_generate(a, g, s), "generation kernel launch");
+    CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
+    sl.ev_recorded = true;
+    return MTGP_OK;
+}
+
+static mtgp_status generate_common(mtgp_streams_t st, const uint32_t* ids, const uint64_t* counts,
+                                   uint32_t n_req, uint32_t fmt, void* out, void* cuda_stream)
+{
+    GUARD_BEGIN
+    if (!st)
+        return fail(MTGP_EINVAL, "null handle");
+    if (fmt > 2)
+        return fail(MTGP_EINVAL, "format %u", fmt);
+    Work w;
+    mtgp_status s = build_work(st->n_streams, ids, counts, nullptr, fmt, n_req, 0, w);
+    if (s != MTGP_OK)
+        return s;
+    if (w.total && !out)
+        return fail(MTGP_EINVAL, "null output pointer");
+    DeviceGuard g(st->device);
+    s = launch_work(st, w, st->cfg, out, (cudaStream_t)cuda_stream);
+    if (s != MTGP_OK)
+        return s;
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_generate_u32(mtgp_streams_t st, const uint32_t* ids, const uint64_t* counts,
+                                         uint32_t n_req, uint32_t* out, void* cuda_stream)
+{
+    return generate_common(st, ids, counts, n_req, MTGP_U32, out, cuda_stream);
+}
+
+extern "C" mtgp_status mtgp_generate_f32(mtgp_streams_t st, const uint32_t* ids, const uint64_t* counts,
+                                         uint32_t n_req, mtgp_format fmt, float* out, void* cuda_stream)
+{
+    return generate_common(st, ids, counts, n_req, (uint32_t)fmt, out, cuda_stream);
+}
+
+extern "C" mtgp_status mtgp_generate_to_host(mtgp_streams_t st, const uint32_t* ids,
+                                             const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
+                                             void* host_out, uint64_t chunk_bytes, void* cuda_stream)
+{
+    GUARD_BEGIN
+    if (!st)
+        return fail(MTGP_EINVAL, "null handle");
+    if ((uint32_t)fmt > 2)
+        return fail(MTGP_EINVAL, "format %d", (int)fmt);
+    if (chunk_bytes == 0)
+        chunk_bytes = 1ull << 30;
+    const uint64_t chunk = std::max<uint64_t>(chunk_bytes / 4, 1024);
+    // validate once over the whole request list
+    {
+        Work w;
+        mtgp_status s = build_work(st->n_streams, ids, counts, nullptr, fmt, n_req, 0, w);
+        if (s != MTGP_OK)
+            return s;
+        if (w.total && !host_out)
+            return fail(MTGP_EINVAL, "null output pointer");
+        if (w.total == 0)
+            return ok();
+    }
+    DeviceGuard g(st->device);
+    cudaStream_t cs = (cudaStream_t)cuda_stream;
+    if (st->stage_cap < chunk) {
+        for (int b = 0; b < 2; ++b) {
+            if (st->stage[b]) {
+                CUDA_TRY(cudaStreamSynchronize(st->copy_stream), "cudaStreamSynchronize");
+                cudaFree(st->stage[b]);
+                st->stage[b] = nullptr;
+            }
+        }
+        st->stage_cap = 0;
+        for (int b = 0; b < 2; ++b)
+            CUDA_TRY(cudaMalloc(&st->stage[b], chunk * 4), "cudaMalloc(staging)");
+        st->stage_cap = chunk;
+    }
+    // Split the request list into chunks of at most `chunk` numbers; a long
+    // request becomes consecutive requests of the same stream, which draw
+    // the same numbers.
+    std::vector<uint32_t> cid;
+    std::vector<uint64_t> ccount;
+    uint64_t host_off = 0;
+    uint64_t fill = 0;
+    int nchunk = 0;
+    bool recorded[2] = {false, false};
+    auto flush = [&]() -> mtgp_status {
+        if (fill == 0)
+            return MTGP_OK;
+        const int b = nchunk & 1;
+        if (recorded[b])
+            CUDA_TRY(cudaStreamWaitEvent(cs, st->ev_copy[b], 0), "cudaStreamWaitEvent");
+        Work w;
+        mtgp_status s = build_work(st->n_streams, cid.data(), ccount.data(), nullptr, fmt,
+                                   (uint32_t)cid.size(), 0, w);
+        if (s != MTGP_OK)
+            return s;
+        s = launch_work(st, w, st->cfg, st->stage[b], cs);
+        if (s != MTGP_OK)
+            return s;
+        CUDA_TRY(cudaEventRecord(st->ev_gen[b], cs), "cudaEventRecord");
+        CUDA_TRY(cudaStreamWaitEvent(st->copy_stream, st->ev_gen[b], 0), "cudaStreamWaitEvent");
+        CUDA_TRY(cudaMemcpyAsync((char*)host_out + host_off * 4, st->stage[b], fill * 4,
+                                 cudaMemcpyDeviceToHost, st->copy_stream),
+                 "cudaMemcpyAsync(D2H)");
+        CUDA_TRY(cudaEventRecord(st->ev_copy[b], st->copy_stream), "cudaEventRecord");
+        recorded[b] = true;
+        host_off += fill;
+        fill = 0;
+        cid.clear();
+        ccount.clear();
+        ++nchunk;
+        return MTGP_OK;
+    };
+    for (uint32_t j = 0; j < n_req; ++j) {
+        uint64_t left = counts[j];
+        while (left) {
+            const uint64_t take = std::min(left, chunk - fill);
+            cid.push_back(ids[j]);
+            ccount.push_back(take);
+            fill += take;
+            left -= take;
+            if (fill == chunk) {
+                mtgp_status s = flush();
+                if (s != MTGP_OK)
+                    return s;
+            }
+        }
+    }
+    mtgp_status s = flush();
+    if (s != MTGP_OK)
+        return s;
+    CUDA_TRY(cudaStreamSynchronize(st->copy_stream), "cudaStreamSynchronize(copy)");
+    CUDA_TRY(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_check(mtgp_streams_t st, void* cuda_stream)
+{
+    GUARD_BEGIN
+    if (!st)
+        return fail(MTGP_EINVAL, "null handle");
+    DeviceGuard g(st->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    int v = 0;
+    CUDA_TRY(cudaMemcpy(&v, st->d_err, sizeof v, cudaMemcpyDeviceToHost), "cudaMemcpy(error word)");
+    if (v) {
+        CUDA_TRY(cudaMemset(st->d_err, 0, sizeof(int)), "cudaMemset");
+        return fail(MTGP_EDEVICE, "a kernel recorded an inconsistent work item (code %d)", v);
+    }
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_streams_free(mtgp_streams_t st)
+{
+    GUARD_BEGIN
+    destroy_streams(st);
+    return ok();
+    GUARD_END
+}
+
+// ---------------------------------------------------------------------------
+// Launch configuration and autotuning
+// ---------------------------------------------------------------------------
+static mtgp_launch_config to_public(const LaunchCfg& c)
+{
+    mtgp_launch_config o;
+    o.warps_per_cta = (uint32_t)c.warps_per_cta;
+    o.ctas_per_sm = (uint32_t)c.ctas_per_sm;
+    o.words_per_lane = (uint32_t)c.k;
+    o.kernel = (uint32_t)c.kernel;
+    return o;
+}
+
+extern "C" mtgp_status mtgp_get_launch_config(mtgp_streams_t st, mtgp_launch_config* cfg)
+{
+    if (!st || !cfg)
+        return fail(MTGP_EINVAL, "null argument");
+    *cfg = to_public(st->cfg);
+    return ok();
+}
+
+mtgp_status mtgp::validate_config(const mtgp_launch_config* c, LaunchCfg* out)
+{
+    if (!c)
+        return fail(MTGP_EINVAL, "null config");
+    if (c->warps_per_cta < 1 || c->warps_per_cta > 8)
+        return fail(MTGP_EINVAL, "warps_per_cta %u not in 1..8", c->warps_per_cta);
+    if (c->words_per_lane != 4 && c->words_per_lane != 8)
+        return fail(MTGP_EINVAL, "words_per_lane %u not 4 or 8", c->words_per_lane);
+    if (c->kernel > 1)
+        return fail(MTGP_EINVAL, "kernel %u not 0 or 1", c->kernel);
+    if (c->ctas_per_sm > 64)
+        return fail(MTGP_EINVAL, "ctas_per_sm %u", c->ctas_per_sm);
+    out->warps_per_cta = (int)c->warps_per_cta;
+    out->ctas_per_sm = (int)c->ctas_per_sm;
+    out->k = (int)c->words_per_lane;
+    out->kernel = (int)c->kernel;
+    return MTGP_OK;
+}
+
+extern "C" mtgp_status mtgp_set_launch_config(mtgp_streams_t st, const mtgp_launch_config* cfg)
+{
+    if (!st)
+        return fail(MTGP_EINVAL, "null handle");
+    LaunchCfg c;
+    mtgp_status s = validate_config(cfg, &c);
+    if (s != MTGP_OK)
+        return s;
+    st->cfg = c;
+    return ok();
+}
+
+std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
+{
+    std::vector<LaunchCfg> v;
+    for (int k : {8, 4}) {
+        if (!fast_supported(P, k))
+            continue;
+        for (int w : {2, 4, 8})
+            for (int c : {0, 4}) {
+                LaunchCfg x;
+                x.warps_per_cta = w;
+                x.ctas_per_sm = c == 0 ? 0 : (c * 4) / w;   // half-occupancy variant
+                x.k = k;
+                x.kernel = 0;
+                v.push_back(x);
+            }
+    }
+    for (int w : {4, 8}) {
+        LaunchCfg x;
+        x.warps_per_cta = w;
+        x.ctas_per_sm = 0;
+        x.k = 8;
+        x.kernel = 1;
+        v.push_back(x);
+    }
+    return v;
+}
+
+// Times one configuration on scratch states: best of `reps` launches.
+mtgp_status mtgp::time_config(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, uint32_t* states,
+                              void* out, int reps, float* best_ms)
+{
+    cudaStream_t s = st->tune_stream;
+    cudaEvent_t a = st->tune_ev[0], b = st->tune_ev[1];
+    uint32_t* saved = st->d_states;
+    st->d_states = states;
+    float best = 1e30f;
+    mtgp_status r = MTGP_OK;
+    for (int i = 0; i < reps + 1 && r == MTGP_OK; ++i) {
+        cudaEventRecord(a, s);
+        r = launch_work(st, w, cfg, out, s);
+        cudaEventRecord(b, s);
+        if (r != MTGP_OK)
+            break;
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) {
+            r = fail_cuda(e, "autotune run");
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (i > 0)
+            best = std::min(best, ms);
+    }
+    st->d_states = saved;
+    *best_ms = best;
+    return r;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, uint32_t, uint32_t, uint32_t>, LaunchCfg> g_tune_cache;
+
+extern "C" mtgp_status mtgp_autotune(mtgp_streams_t st, mtgp_format fmt, uint32_t sample_streams,
+                                     uint64_t sample_count, mtgp_launch_config* best)
+{
+    GUARD_BEGIN
+    if (!st)
+        return fail(MTGP_EINVAL, "null handle");
+    if ((uint32_t)fmt > 2)
+        return fail(MTGP_EINVAL, "format");
+    DeviceGuard g(st->device);
+    const auto key = std::make_tuple(st->device, st->P.k.n, st->P.k.pos, (uint32_t)fmt);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            st->cfg = it->second;
+            if (best)
+                *best = to_public(st->cfg);
+            return ok();
+        }
+    }
+    if (sample_streams == 0)
+        sample_streams = 4096;
+    if (sample_count == 0)
+        sample_count = 1u << 14;
+    const uint32_t ns = std::min(sample_streams, st->n_streams);
+    const size_t np = st->P.k.np;
+    uint32_t* scratch = nullptr;
+    void* out = nullptr;
+    CUDA_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    CUDA_TRY(cudaMalloc(&scratch, (size_t)ns * np * 4), "cudaMalloc(tune states)");
+    cudaError_t e = cudaMalloc(&out, (size_t)ns * sample_count * 4);
+    if (e != cudaSuccess) {
+        cudaFree(scratch);
+        return fail_cuda(e, "cudaMalloc(tune output)");
+    }
+    mtgp_status r = MTGP_OK;
+    LaunchCfg win = st->cfg;
+    if ((e = cudaMemcpy(scratch, st->d_states, (size_t)ns * np * 4, cudaMemcpyDeviceToDevice)) !=
+        cudaSuccess)
+        r = fail_cuda(e, "cudaMemcpy(tune states)");
+    if (r == MTGP_OK && !st->tune_stream) {
+        if ((e = cudaStreamCreateWithFlags(&st->tune_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreate(&st->tune_ev[0])) != cudaSuccess ||
+            (e = cudaEventCreate(&st->tune_ev[1])) != cudaSuccess)
+            r = fail_cuda(e, "tune stream/events");
+    }
+    if (r == MTGP_OK) {
+        std::vector<uint32_t> ids(ns);
+        std::vector<uint64_t> cnt(ns, sample_count);
+        for (uint32_t i = 0; i < ns; ++i)
+            ids[i] = i;
+        Work w;
+        // scratch holds the first ns states, so ids stay below ns
+        const uint32_t saved_n = st->n_streams;
+        st->n_streams = ns;
+        r = build_work(ns, ids.data(), cnt.data(), nullptr, (uint32_t)fmt, ns, 0, w);
+        float best_ms = 1e30f;
+        if (r == MTGP_OK) {
+            for (const LaunchCfg& c : tuning_candidates(st->P.k)) {
+                float ms = 0;
+                r = time_config(st, w, c, scratch, out, 2, &ms);
+                if (r != MTGP_OK)
+                    break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    win = c;
+                }
+            }
+        }
+        st->n_streams = saved_n;
+    }
+    cudaStreamSynchronize(st->tune_stream);
+    cudaFree(scratch);
+    cudaFree(out);
+    if (r != MTGP_OK)
+        return r;
+    st->cfg = win;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = win;
+    }
+    if (best)
+        *best = to_public(win);
+    return ok();
+    GUARD_END
+}
+
+// ---------------------------------------------------------------------------
+// Plans (one persistent launch recorded as a CUDA graph)
+// ---------------------------------------------------------------------------
+static mtgp_status record_graph(mtgp_plan* p)
+{
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    if (p->graph) {
+        cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    p->kernel_launches = 0;
+    if (p->n_items == 0)
+        return MTGP_OK;
+    cudaStream_t cap = p->cap_stream;
+    CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t e1 = cudaMemsetAsync(p->d_table, 0, sizeof(uint32_t), cap);
+    GenArgs a;
+    a.P = p->st->P.k;
+    a.states = p->st->d_states;
+    a.n_streams = p->st->n_streams;
+    a.items = (const WorkItem*)((char*)p->d_table + p->items_off);
+    a.segs = (const Segment*)((char*)p->d_table + p->segs_off);
+    a.n_items = p->n_items;
+    a.counter = (uint32_t*)p->d_table;
+    a.out = (uint32_t*)p->out;
+    a.err = p->st->d_err;
+    cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, p->geo, cap) : e1;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(cap, &graph);
+    if (e2 != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return fail_cuda(e2, "plan capture");
+    }
+    if (e3 != cudaSuccess)
+        return fail_cuda(e3, "cudaStreamEndCapture");
+    p->graph = graph;
+    CUDA_TRY(cudaGraphInstantiate(&p->exec, graph, 0), "cudaGraphInstantiate");
+    p->kernel_launches = 1;
+    return MTGP_OK;
+}
+
+static void destroy_plan(mtgp_plan* p)
+{
+    if (!p)
+        return;
+    DeviceGuard g(p->st->device);
+    if (p->exec)
+        cudaGraphExecDestroy(p->exec);
+    if (p->graph)
+        cudaGraphDestroy(p->graph);
+    if (p->cap_stream)
+        cudaStreamDestroy(p->cap_stream);
+    if (p->d_table)
+        cudaFree(p->d_table);
+    delete p;
+}
+
+extern "C" mtgp_status mtgp_plan_create(mtgp_streams_t st, const uint32_t* ids, const uint64_t* counts,
+                                        uint32_t n_req, mtgp_format fmt, void* out, mtgp_plan_t* plan)
+{
+    GUARD_BEGIN
+    if (!st || !plan)
+        return fail(MTGP_EINVAL, "null argument");
+    if ((uint32_t)fmt > 2)
+        return fail(MTGP_EINVAL, "format");
+    Work w;
+    mtgp_status s = build_work(st->n_streams, ids, counts, nullptr, (uint32_t)fmt, n_req, 0, w);
+    if (s != MTGP_OK)
+        return s;
+    if (w.total && !out)
+        return fail(MTGP_EINVAL, "null output pointer");
+    DeviceGuard g(st->device);
+    mtgp_plan* p = new mtgp_plan;
+    p->st = st;
+    p->out = out;
+    p->n_items = (uint32_t)w.items.size();
+    p->total = w.total;
+    p->max_item = w.max_item;
+    p->cfg = st->cfg;
+    p->work = w;
+    auto bail = [&](mtgp_status r) {
+        destroy_plan(p);
+        return r;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaStreamCreate"));
+    const size_t bytes = table_bytes(w, &p->items_off, &p->segs_off);
+    std::vector<char> host(bytes);
+    fill_table(w, host.data());
+    if ((e = cudaMalloc(&p->d_table, bytes)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMalloc(plan table)"));
+    if ((e = cudaMemcpy(p->d_table, host.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMemcpy(plan table)"));
+    s = geometry_for(st, p->cfg, p->n_items, &p->geo);
+    if (s != MTGP_OK)
+        return bail(s);
+    s = record_graph(p);
+    if (s != MTGP_OK)
+        return bail(s);
+    *plan = p;
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_plan_launch(mtgp_plan_t p, void* cuda_stream)
+{
+    if (!p)
+        return fail(MTGP_EINVAL, "null plan");
+    if (!p->exec)
+        return ok();
+    DeviceGuard g(p->st->device);
+    CUDA_TRY(cudaGraphLaunch(p->exec, (cudaStream_t)cuda_stream), "cudaGraphLaunch");
+    return ok();
+}
+
+extern "C" mtgp_status mtgp_plan_autotune(mtgp_plan_t p, mtgp_launch_config* best)
+{
+    GUARD_BEGIN
+    if (!p)
+        return fail(MTGP_EINVAL, "null plan");
+    mtgp_streams* st = p->st;
+    DeviceGuard g(st->device);
+    if (p->n_items == 0) {
+        if (best)
+            *best = to_public(p->cfg);
+        return ok();
+    }
+    const size_t bytes = (size_t)st->n_streams * st->P.k.np * 4;
+    uint32_t* scratch = nullptr;
+    CUDA_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    CUDA_TRY(cudaMalloc(&scratch, bytes), "cudaMalloc(tune states)");
+    cudaError_t e = cudaMemcpy(scratch, st->d_states, bytes, cudaMemcpyDeviceToDevice);
+    mtgp_status r = e == cudaSuccess ? MTGP_OK : fail_cuda(e, "cudaMemcpy(tune states)");
+    if (r == MTGP_OK && !st->tune_stream) {
+        if ((e = cudaStreamCreateWithFlags(&st->tune_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreate(&st->tune_ev[0])) != cudaSuccess ||
+            (e = cudaEventCreate(&st->tune_ev[1])) != cudaSuccess)
+            r = fail_cuda(e, "tune stream/events");
+    }
+    LaunchCfg win = p->cfg;
+    float best_ms = 1e30f;
+    if (r == MTGP_OK) {
+        for (const LaunchCfg& c : tuning_candidates(st->P.k)) {
+            float ms = 0;
+            r = time_config(st, p->work, c, scratch, p->out, 2, &ms);
+            if (r != MTGP_OK)
+                break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                win = c;
+            }
+        }
+    }
+    cudaStreamSynchronize(st->tune_stream);
+    cudaFree(scratch);
+    if (r != MTGP_OK)
+        return r;
+    p->cfg = win;
+    r = geometry_for(st, p->cfg, p->n_items, &p->geo);
+    if (r != MTGP_OK)
+        return r;
+    r = record_graph(p);
+    if (r != MTGP_OK)
+        return r;
+    if (best)
+        *best = to_public(win);
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_plan_get_info(mtgp_plan_t p, mtgp_plan_info* info)
+{
+    if (!p || !info)
+        return fail(MTGP_EINVAL, "null argument");
+    info->total_numbers = p->total;
+    info->n_items = p->n_items;
+    info->kernel_launches = p->kernel_launches;
+    LaunchCfg eff = p->cfg;
+    eff.kernel = p->geo.kernel;
+    eff.k = p->geo.k;
+    info->config = to_public(eff);
+    info->grid_ctas = (uint32_t)p->geo.grid;
+    return ok();
+}
+
+extern "C" mtgp_status mtgp_plan_free(mtgp_plan_t p)
+{
+    GUARD_BEGIN
+    destroy_plan(p);
+    return ok();
+    GUARD_END
+}
+
+extern "C" const char* mtgp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* mtgp_version(void) { return "libmtgp 0.1 (sm_103a)"; }

@@ -1,0 +1,20 @@
+// Instantiations of the register-resident kernel for M = ceil(N/32) in {20,22,23}
+// (state sizes of the common MTGP32 exponents; see mtgp_fast.cuh).
+#include "mtgp_fast.cuh"
+
+namespace mtgp {
+
+const void* fast_ptr_group_b(int M, int K)
+{
+    switch (M * 16 + K) {
+    case 20 * 16 + 4: return (const void*)mtgp_fast_kernel<20, 4>;
+    case 20 * 16 + 8: return (const void*)mtgp_fast_kernel<20, 8>;
+    case 22 * 16 + 4: return (const void*)mtgp_fast_kernel<22, 4>;
+    case 22 * 16 + 8: return (const void*)mtgp_fast_kernel<22, 8>;
+    case 23 * 16 + 4: return (const void*)mtgp_fast_kernel<23, 4>;
+    case 23 * 16 + 8: return (const void*)mtgp_fast_kernel<23, 8>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace mtgp

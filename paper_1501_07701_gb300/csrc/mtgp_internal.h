@@ -1,0 +1,103 @@
+// Internal declarations shared by the host runtime (mtgp_api.cpp,
+// mtgp_server.cpp) and the kernels (mtgp_kernels.cu, mtgp_fast_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mtgp {
+
+// Parameterized status in the form the kernels take it (by value, so it
+// lives in the kernel-parameter constant bank).  flt[k] = (tmp[k] >> 9) |
+// 0x3F800000 is the precomputed float tempering table of a "fast" status:
+// (x >> 9) ^ flt[k] is the [1,2) bit pattern of x ^ tmp[k].
+struct KParams {
+    uint32_t n;      // state words N
+    uint32_t np;     // HBM row stride in words: N rounded up to 4 (16-byte rows)
+    uint32_t pos, sh1, sh2, mask;
+    uint32_t rec[16];
+    uint32_t tmp[16];
+    uint32_t flt[16];
+};
+
+// One stream touched by a launch.  Its requests are the segments
+// [seg_begin, seg_begin + nseg); they are generated back to back, so the
+// stream's output index g runs over 0 .. total-1 across its segments.
+struct WorkItem {
+    uint32_t stream;
+    uint32_t seg_begin;
+    uint32_t nseg;
+    uint32_t pad;
+};
+
+// One request of a stream: numbers g in [g_start, g_start + count) of the
+// item go to out[out_off + (g - g_start)] in format fmt (0 u32, 1 f32 [1,2),
+// 2 f32 [0,1)).
+struct Segment {
+    uint64_t g_start;
+    uint64_t count;
+    uint64_t out_off;
+    uint32_t fmt;
+    uint32_t pad;
+};
+
+struct LaunchCfg {
+    int warps_per_cta;   // 1..8
+    int ctas_per_sm;     // 0 = occupancy maximum
+    int k;               // sub-steps per parallel step (words per lane), 4 or 8
+    int kernel;          // 0 register-resident, 1 shared-memory ring
+};
+
+// Per-warp shared-memory footprint (32-bit words).
+//   fast: 3 pad words + guard S[-1], then S[0 .. N+32) rounded up to 4 words,
+//         so that S is 16-byte aligned for the cp.async stage-in.
+//   ring: S[0 .. N) rounded up to 4 words.
+__host__ __device__ inline uint32_t fast_smem_words(uint32_t n) { return 4u + ((n + 32u + 3u) & ~3u); }
+__host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return (n + 3u) & ~3u; }
+
+// True if the register-resident kernel has an instantiation for this N and
+// the window 32*k fits: 32*k <= N - pos.
+bool fast_supported(const KParams& P, int k);
+
+// Seed status -> state rows (row stride P.np words; padding words zeroed).
+cudaError_t launch_init(const KParams& P, const uint32_t* d_seeds, uint32_t n_streams,
+                        uint32_t* d_states, cudaStream_t s);
+
+struct GenArgs {
+    KParams P;
+    uint32_t* states;
+    uint32_t n_streams;
+    const WorkItem* items;
+    const Segment* segs;
+    uint32_t n_items;
+    uint32_t* counter;   // zeroed before the launch
+    uint32_t* out;
+    int* err;
+};
+
+// Resolved launch geometry for a configuration.
+struct Geometry {
+    int kernel;          // kernel actually used (fast falls back to ring)
+    int k;
+    int threads;
+    size_t smem;
+    int grid;
+};
+
+// Works out kernel choice, block size, shared memory and grid (persistent:
+// at most num_sms * resident CTAs, at least enough warps for n_items when
+// fewer).  Returns cudaSuccess or the occupancy query's error.
+cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_items, int device,
+                          Geometry* g);
+
+// Launches the generation kernel described by `g` (counter must be zero).
+cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s);
+
+// Fast-kernel launchers, one translation unit per group of state sizes.
+// M = ceil(N / 32) register columns per lane; returns cudaErrorInvalidValue
+// if M or K has no instantiation.
+cudaError_t launch_fast(int M, int K, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
+                        cudaStream_t s);
+const void* fast_kernel_ptr(int M, int K);
+
+}  // namespace mtgp

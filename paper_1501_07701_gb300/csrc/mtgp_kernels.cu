@@ -1,0 +1,274 @@
+// Status initialisation, the shared-memory ring kernel (any parameter set),
+// and launch geometry for MTGP32 generation on sm_103a.
+#include <algorithm>
+
+#include "mtgp_internal.h"
+
+namespace mtgp {
+
+// ---------------------------------------------------------------------------
+// Seed status -> state (Sec. 3.1 "seed status"; the MT-family seeding
+// recurrence w_i = 1812433253 * (w_{i-1} ^ (w_{i-1} >> 30)) + i).  The
+// recurrence is sequential within a stream, so one thread owns one stream;
+// it stages its words through shared memory so that a warp writes 32
+// consecutive words of one row at a time.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) mtgp_init_kernel(const uint32_t* __restrict__ seeds,
+                                                        uint32_t n_streams, uint32_t n, uint32_t np,
+                                                        uint32_t* __restrict__ states)
+{
+    __shared__ uint32_t buf[4][32][33];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t s0 = (blockIdx.x * 4u + warp) * 32u;   // first stream of this warp
+    const uint32_t s = s0 + lane;
+    uint32_t w = s < n_streams ? seeds[s] : 0u;
+    for (uint32_t c0 = 0; c0 < np; c0 += 32u) {
+        // each lane produces words c0..c0+31 of its own stream
+        for (uint32_t j = 0; j < 32u; ++j) {
+            const uint32_t i = c0 + j;
+            uint32_t v = 0;
+            if (i == 0)
+                v = w;
+            else if (i < n) {
+                w = 1812433253u * (w ^ (w >> 30)) + i;
+                v = w;
+            }
+            buf[warp][lane][j] = v;
+        }
+        __syncwarp();
+        // warp writes row by row: lane j writes word c0+j of stream s0+t
+        for (uint32_t t = 0; t < 32u; ++t) {
+            const uint32_t st = s0 + t;
+            const uint32_t i = c0 + lane;
+            if (st < n_streams && i < np)
+                states[(size_t)st * np + i] = buf[warp][t][lane];
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_init(const KParams& P, const uint32_t* d_seeds, uint32_t n_streams,
+                        uint32_t* d_states, cudaStream_t s)
+{
+    if (n_streams == 0)
+        return cudaSuccess;
+    const uint32_t blocks = (n_streams + 127u) / 128u;
+    mtgp_init_kernel<<<blocks, 128, 0, s>>>(d_seeds, n_streams, P.n, P.np, d_states);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory ring kernel: any N >= 2 and any pos.  One warp per stream;
+// the state row S[0..N) holds the latest value of each column (column c of
+// row q is x_{qN+c}).  Each parallel step computes Wc = min(32, N - pos)
+// consecutive columns: every word it reads was produced before the step.
+// Every output lane finds its own request, so this kernel also serves as the
+// plain reference path for unusual parameter sets.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_t* __restrict__ states,
+                                                        uint32_t n_streams,
+                                                        const WorkItem* __restrict__ items,
+                                                        const Segment* __restrict__ segs,
+                                                        uint32_t n_items, uint32_t* __restrict__ counter,
+                                                        uint32_t* __restrict__ out, int* __restrict__ err)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t* rec = smem;
+    uint32_t* tmp = smem + 16;
+    if (threadIdx.x < 16) {
+        rec[threadIdx.x] = P.rec[threadIdx.x];
+        tmp[threadIdx.x] = P.tmp[threadIdx.x];
+    }
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t N = P.n, pos = P.pos;
+    uint32_t* S = smem + 32 + warp * ring_smem_words(N);
+    const uint32_t Wc = (N - pos) < 32u ? (N - pos) : 32u;
+
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0)
+            it = atomicAdd(counter, 1u);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= n_items)
+            break;
+        const WorkItem w = items[it];
+        if (w.stream >= n_streams || w.nseg == 0) {
+            if (lane == 0)
+                atomicOr(err, 1);
+            continue;
+        }
+        uint32_t* g = states + (size_t)w.stream * P.np;
+        for (uint32_t j = lane; j < N; j += 32u)
+            S[j] = g[j];
+        __syncwarp();
+
+        const uint32_t s_end = w.seg_begin + w.nseg;
+        const Segment last = segs[s_end - 1u];
+        const uint64_t total = last.g_start + last.count;
+        uint32_t s_row = w.seg_begin;
+        for (uint64_t row = 0; row < total; row += N) {
+            while (segs[s_row].g_start + segs[s_row].count <= row)
+                ++s_row;
+            const uint64_t left = total - row;
+            const uint32_t n_valid = left < (uint64_t)N ? (uint32_t)left : N;
+            for (uint32_t c0 = 0; c0 < n_valid; c0 += Wc) {
+                const uint32_t c = c0 + lane;
+                const bool act = lane < Wc && c < n_valid;
+                uint32_t xn = 0, o = 0;
+                if (act) {
+                    const uint32_t c1 = (c + 1u == N) ? 0u : c + 1u;
+                    uint32_t cp = c + pos;
+                    cp = cp >= N ? cp - N : cp;
+                    uint32_t cq = c + pos - 1u;
+                    cq = cq >= N ? cq - N : cq;
+                    uint32_t y = (S[c] & P.mask) ^ S[c1];
+                    y ^= y << P.sh1;
+                    y ^= S[cp] >> P.sh2;
+                    xn = y ^ rec[y & 15u];
+                    uint32_t t = S[cq];
+                    t ^= t >> 16;
+                    t ^= t >> 8;
+                    o = xn ^ tmp[t & 15u];
+                }
+                __syncwarp();
+                if (act) {
+                    S[c] = xn;
+                    const uint64_t gi = row + c;
+                    uint32_t s = s_row;
+                    while (s + 1u < s_end && gi >= segs[s + 1u].g_start)
+                        ++s;
+                    const Segment sg = segs[s];
+                    if (sg.fmt != 0) {
+                        const uint32_t b = 0x3F800000u | (o >> 9);
+                        o = sg.fmt == 1 ? b : __float_as_uint(__uint_as_float(b) - 1.0f);
+                    }
+                    out[sg.out_off + (gi - sg.g_start)] = o;
+                }
+                __syncwarp();
+            }
+        }
+        const uint32_t phase = (uint32_t)(total % N);
+        for (uint32_t j = lane; j < N; j += 32u) {
+            uint32_t c = phase + j;
+            c = c >= N ? c - N : c;
+            g[j] = S[c];
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry and dispatch
+// ---------------------------------------------------------------------------
+static int fast_m(const KParams& P) { return (int)((P.n + 31u) / 32u); }
+
+bool fast_supported(const KParams& P, int k)
+{
+    if (k != 4 && k != 8)
+        return false;
+    if (P.n < 64 || 32u * (uint32_t)k > P.n - P.pos)
+        return false;
+    const int M = fast_m(P);
+    if (M <= k)
+        return false;
+    return fast_kernel_ptr(M, k) != nullptr;
+}
+
+cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_items, int device,
+                          Geometry* g)
+{
+    int k = cfg.k;
+    int kernel = cfg.kernel;
+    if (kernel == 0 && !fast_supported(P, k)) {
+        if (k == 8 && fast_supported(P, 4))
+            k = 4;
+        else
+            kernel = 1;
+    }
+    const int warps = std::max(1, std::min(8, cfg.warps_per_cta));
+    g->kernel = kernel;
+    g->k = k;
+    g->threads = warps * 32;
+    const void* fn;
+    if (kernel == 0) {
+        g->smem = (size_t)warps * fast_smem_words(P.n) * 4u;
+        fn = fast_kernel_ptr(fast_m(P), k);
+    } else {
+        g->smem = (size_t)(32u + warps * ring_smem_words(P.n)) * 4u;
+        fn = (const void*)mtgp_ring_kernel;
+    }
+    cudaError_t e;
+    if (g->smem > 48u * 1024u) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g->threads, g->smem);
+    if (e != cudaSuccess)
+        return e;
+    if (per_sm < 1)
+        return cudaErrorInvalidConfiguration;
+    if (cfg.ctas_per_sm > 0)
+        per_sm = std::min(per_sm, cfg.ctas_per_sm);
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess)
+        return e;
+    const long long want = ((long long)n_items + warps - 1) / warps;
+    const long long cap = (long long)sms * per_sm;
+    g->grid = (int)std::max(1LL, std::min(want, cap));
+    return cudaSuccess;
+}
+
+cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
+{
+    if (a.n_items == 0)
+        return cudaSuccess;
+    if (g.kernel == 0)
+        return launch_fast((int)((a.P.n + 31u) / 32u), g.k, a, dim3(g.grid), dim3(g.threads), g.smem, s);
+    mtgp_ring_kernel<<<g.grid, g.threads, g.smem, s>>>(a.P, a.states, a.n_streams, a.items, a.segs,
+                                                       a.n_items, a.counter, a.out, a.err);
+    return cudaGetLastError();
+}
+
+}  // namespace mtgp
+
+namespace mtgp {
+
+const void* fast_ptr_group_a(int M, int K);
+const void* fast_ptr_group_b(int M, int K);
+const void* fast_ptr_group_c(int M, int K);
+
+const void* fast_kernel_ptr(int M, int K)
+{
+    const void* p = fast_ptr_group_a(M, K);
+    if (!p)
+        p = fast_ptr_group_b(M, K);
+    if (!p)
+        p = fast_ptr_group_c(M, K);
+    return p;
+}
+
+cudaError_t launch_fast(int M, int K, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
+                        cudaStream_t s)
+{
+    const void* fn = fast_kernel_ptr(M, K);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    KParams P = a.P;
+    uint32_t* states = a.states;
+    uint32_t n_streams = a.n_streams;
+    const WorkItem* items = a.items;
+    const Segment* segs = a.segs;
+    uint32_t n_items = a.n_items;
+    uint32_t* counter = a.counter;
+    uint32_t* out = a.out;
+    int* err = a.err;
+    void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &counter, &out, &err};
+    return cudaLaunchKernel(fn, grid, block, args, smem, s);
+}
+
+}  // namespace mtgp

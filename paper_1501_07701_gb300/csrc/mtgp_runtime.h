@@ -1,0 +1,110 @@
+// Host-side runtime structures behind the C ABI (not part of the public
+// interface).
+#pragma once
+
+#include <array>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mtgp.h"
+#include "mtgp_internal.h"
+
+#define MTGP_MAX_N 16384u
+
+struct mtgp_params {
+    mtgp_params_desc d;   // completed fields
+    mtgp::KParams k;      // kernel form (with the float tempering table)
+};
+
+namespace mtgp {
+
+// Requests grouped per stream (in request order), streams sorted by total
+// count, longest first.
+struct Work {
+    std::vector<WorkItem> items;
+    std::vector<Segment> segs;
+    uint64_t total = 0;
+    uint64_t max_item = 0;
+};
+
+// A pinned host buffer and a device buffer holding one uploaded work table
+// (work counter, items, segments); `ev` marks the end of the kernel that
+// consumed it, so the slot can be refilled.
+struct TableSlot {
+    void* host = nullptr;
+    void* dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool ev_recorded = false;
+};
+
+struct DeviceGuard {
+    int prev;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+mtgp_status fail(mtgp_status st, const char* fmt, ...);
+mtgp_status fail_cuda(cudaError_t e, const char* what);
+mtgp_status ok();
+
+}  // namespace mtgp
+
+struct mtgp_streams {
+    mtgp_params P;
+    int device = 0;
+    uint32_t n_streams = 0;
+    uint32_t* d_states = nullptr;   // n_streams rows of P.k.np words
+    int* d_err = nullptr;           // device error word
+    mtgp::LaunchCfg cfg{};
+    std::array<mtgp::TableSlot, 4> slots{};
+    int next_slot = 0;
+    // launch geometry cache (for the current cfg; grid = residency cap)
+    bool geo_valid = false;
+    std::tuple<int, int, int, int> geo_key{};
+    mtgp::Geometry geo_cap{};
+    // device-to-host path
+    void* stage[2] = {nullptr, nullptr};
+    uint64_t stage_cap = 0;   // elements per staging buffer
+    cudaEvent_t ev_gen[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    // autotuning
+    cudaStream_t tune_stream = nullptr;
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+};
+
+struct mtgp_plan {
+    mtgp_streams* st = nullptr;
+    void* out = nullptr;
+    uint32_t n_items = 0;
+    uint64_t total = 0;
+    uint64_t max_item = 0;
+    mtgp::LaunchCfg cfg{};
+    mtgp::Geometry geo{};
+    mtgp::Work work;
+    void* d_table = nullptr;
+    size_t items_off = 0, segs_off = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t kernel_launches = 0;
+};
+
+namespace mtgp {
+
+mtgp_status build_work(uint32_t n_streams, const uint32_t* ids, const uint64_t* counts,
+                       const int32_t* fmts, uint32_t fmt_all, uint32_t n_req, uint64_t out_base,
+                       Work& w);
+size_t table_bytes(const Work& w, size_t* items_off, size_t* segs_off);
+void fill_table(const Work& w, void* host);
+LaunchCfg default_config(const KParams& P);
+mtgp_status geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t n_items, Geometry* g);
+mtgp_status launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
+                        cudaStream_t s);
+mtgp_status validate_config(const mtgp_launch_config* c, LaunchCfg* out);
+std::vector<LaunchCfg> tuning_candidates(const KParams& P);
+mtgp_status time_config(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, uint32_t* states,
+                        void* out, int reps, float* best_ms);
+
+}  // namespace mtgp

@@ -1,0 +1,361 @@
+"""Python binding of libmtgp (ctypes): argument marshalling only.
+
+Every function keeps the name of the C entry point it calls (include/mtgp.h).
+Device buffers are torch CUDA tensors (any 4-byte dtype) or raw integer
+pointers; streams are torch.cuda.Stream objects, raw cudaStream_t integers,
+or None for torch's current stream.  All generation work runs in the CUDA
+kernels of libmtgp.so; if the library is missing this module raises instead
+of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmtgp.so")
+
+MTGP_U32, MTGP_F32_12, MTGP_F32_01 = 0, 1, 2
+STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
+                4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY", 6: "MTGP_EIO", 7: "MTGP_EDEVICE"}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class MtgpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class ParamsDesc(ctypes.Structure):
+    _fields_ = [("mexp", ctypes.c_uint32), ("n", ctypes.c_uint32), ("pos", ctypes.c_uint32),
+                ("sh1", ctypes.c_uint32), ("sh2", ctypes.c_uint32), ("mask", ctypes.c_uint32),
+                ("rec_tbl", ctypes.c_uint32 * 16), ("tmp_tbl", ctypes.c_uint32 * 16)]
+
+
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("words_per_lane", ctypes.c_uint32), ("kernel", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("total_numbers", ctypes.c_uint64), ("n_items", ctypes.c_uint32),
+                ("kernel_launches", ctypes.c_uint32), ("config", LaunchConfig),
+                ("grid_ctas", ctypes.c_uint32)]
+
+
+_VP = ctypes.c_void_p
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+
+# name -> argtypes (restype int status unless listed in _STR)
+_SIGS = {
+    "mtgp_params_load": [ctypes.c_char_p, ctypes.POINTER(_VP)],
+    "mtgp_params_generate": [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(_VP)],
+    "mtgp_params_create": [ctypes.POINTER(ParamsDesc), ctypes.POINTER(_VP)],
+    "mtgp_params_get": [_VP, ctypes.POINTER(ParamsDesc)],
+    "mtgp_params_free": [_VP],
+    "mtgp_init_statuses": [_VP, _U32P, ctypes.c_uint32, _VP, ctypes.POINTER(_VP)],
+    "mtgp_set_statuses": [_VP, _U32P, _VP],
+    "mtgp_get_statuses": [_VP, _U32P, _VP],
+    "mtgp_streams_info": [_VP, _U32P, _U32P],
+    "mtgp_generate_u32": [_VP, _U32P, _U64P, ctypes.c_uint32, _VP, _VP],
+    "mtgp_generate_f32": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP, _VP],
+    "mtgp_generate_to_host": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP,
+                              ctypes.c_uint64, _VP],
+    "mtgp_check": [_VP, _VP],
+    "mtgp_streams_free": [_VP],
+    "mtgp_get_launch_config": [_VP, ctypes.POINTER(LaunchConfig)],
+    "mtgp_set_launch_config": [_VP, ctypes.POINTER(LaunchConfig)],
+    "mtgp_autotune": [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                      ctypes.POINTER(LaunchConfig)],
+    "mtgp_plan_create": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP,
+                         ctypes.POINTER(_VP)],
+    "mtgp_plan_launch": [_VP, _VP],
+    "mtgp_plan_autotune": [_VP, ctypes.POINTER(LaunchConfig)],
+    "mtgp_plan_get_info": [_VP, ctypes.POINTER(PlanInfo)],
+    "mtgp_plan_free": [_VP],
+    "mtgp_last_error": [],
+    "mtgp_version": [],
+}
+_STR = {"mtgp_last_error", "mtgp_version"}
+
+
+def load_library(path: str | None = None):
+    """Loads libmtgp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError("libmtgp.so not found at %s; build it with "
+                                   "paper_1501_07701_gb300.build.build()" % p)
+            lib = ctypes.CDLL(p)
+            for name, args in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = ctypes.c_char_p if name in _STR else ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _call(name, *args):
+    lib = load_library()
+    st = getattr(lib, name)(*args)
+    if st != 0:
+        raise MtgpError(st, lib.mtgp_last_error().decode())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(buf, min_elems: int = 0):
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    import torch
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda:
+        raise TypeError("device buffer must be a CUDA tensor or an integer pointer")
+    if buf.element_size() != 4 or not buf.is_contiguous():
+        raise TypeError("device buffer must be contiguous with 4-byte elements")
+    if buf.numel() < min_elems:
+        raise ValueError("device buffer holds %d elements, %d needed" % (buf.numel(), min_elems))
+    return buf.data_ptr()
+
+
+def _req_arrays(ids, counts):
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    if ids.shape != counts.shape or ids.ndim != 1:
+        raise ValueError("stream_ids and counts must be 1-D arrays of equal length")
+    return ids, counts
+
+
+def _p32(a):
+    return a.ctypes.data_as(_U32P)
+
+
+def _p64(a):
+    return a.ctypes.data_as(_U64P)
+
+
+class Params:
+    """Owning wrapper of an mtgp_params_t."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            _call("mtgp_params_free", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Streams:
+    """Owning wrapper of an mtgp_streams_t."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @property
+    def n_streams(self):
+        return mtgp_streams_info(self)[0]
+
+    @property
+    def n_words(self):
+        return mtgp_streams_info(self)[1]
+
+    def close(self):
+        if self.handle:
+            _call("mtgp_streams_free", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Owning wrapper of an mtgp_plan_t (keeps its Streams alive)."""
+
+    def __init__(self, handle, streams, out):
+        self.handle = handle
+        self.streams = streams
+        self.out = out
+
+    def close(self):
+        if self.handle:
+            _call("mtgp_plan_free", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mtgp_version():
+    return load_library().mtgp_version().decode()
+
+
+def mtgp_params_load(path: str) -> Params:
+    h = _VP()
+    _call("mtgp_params_load", path.encode(), ctypes.byref(h))
+    return Params(h)
+
+
+def mtgp_params_generate(mexp: int, seed: int) -> Params:
+    h = _VP()
+    _call("mtgp_params_generate", mexp, seed, ctypes.byref(h))
+    return Params(h)
+
+
+def mtgp_params_create(mexp, pos, sh1, sh2, rec_tbl, tmp_tbl, n=0, mask=0) -> Params:
+    d = ParamsDesc()
+    d.mexp, d.n, d.pos, d.sh1, d.sh2, d.mask = mexp, n, pos, sh1, sh2, mask
+    for i in range(16):
+        d.rec_tbl[i] = int(rec_tbl[i]) & 0xFFFFFFFF
+        d.tmp_tbl[i] = int(tmp_tbl[i]) & 0xFFFFFFFF
+    h = _VP()
+    _call("mtgp_params_create", ctypes.byref(d), ctypes.byref(h))
+    return Params(h)
+
+
+def mtgp_params_get(params: Params) -> dict:
+    d = ParamsDesc()
+    _call("mtgp_params_get", params.handle, ctypes.byref(d))
+    return {"mexp": d.mexp, "n": d.n, "pos": d.pos, "sh1": d.sh1, "sh2": d.sh2, "mask": d.mask,
+            "rec_tbl": list(d.rec_tbl), "tmp_tbl": list(d.tmp_tbl)}
+
+
+def mtgp_init_statuses(params: Params, seeds, stream=None) -> Streams:
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+    h = _VP()
+    _call("mtgp_init_statuses", params.handle, _p32(seeds), seeds.size, _stream_handle(stream),
+          ctypes.byref(h))
+    return Streams(h)
+
+
+def mtgp_streams_info(streams: Streams):
+    n, w = ctypes.c_uint32(), ctypes.c_uint32()
+    _call("mtgp_streams_info", streams.handle, ctypes.byref(n), ctypes.byref(w))
+    return n.value, w.value
+
+
+def mtgp_set_statuses(streams: Streams, states, stream=None):
+    n, w = mtgp_streams_info(streams)
+    states = np.ascontiguousarray(states, dtype=np.uint32)
+    if states.shape != (n, w):
+        raise ValueError("states must have shape (%d, %d)" % (n, w))
+    _call("mtgp_set_statuses", streams.handle, _p32(states), _stream_handle(stream))
+
+
+def mtgp_get_statuses(streams: Streams, stream=None) -> np.ndarray:
+    n, w = mtgp_streams_info(streams)
+    out = np.zeros((n, w), np.uint32)
+    _call("mtgp_get_statuses", streams.handle, _p32(out), _stream_handle(stream))
+    return out
+
+
+def mtgp_generate_u32(streams: Streams, stream_ids, counts, out, stream=None):
+    ids, counts = _req_arrays(stream_ids, counts)
+    total = int(counts.sum()) if counts.size else 0
+    _call("mtgp_generate_u32", streams.handle, _p32(ids), _p64(counts), ids.size,
+          _dev_ptr(out, total), _stream_handle(stream))
+
+
+def mtgp_generate_f32(streams: Streams, stream_ids, counts, fmt, out, stream=None):
+    ids, counts = _req_arrays(stream_ids, counts)
+    total = int(counts.sum()) if counts.size else 0
+    _call("mtgp_generate_f32", streams.handle, _p32(ids), _p64(counts), ids.size, int(fmt),
+          _dev_ptr(out, total), _stream_handle(stream))
+
+
+def mtgp_generate_to_host(streams: Streams, stream_ids, counts, fmt, host_out, chunk_bytes=0,
+                          stream=None):
+    """host_out: a NumPy array or a CPU torch tensor (pinned for full speed)."""
+    ids, counts = _req_arrays(stream_ids, counts)
+    total = int(counts.sum()) if counts.size else 0
+    if isinstance(host_out, np.ndarray):
+        if host_out.itemsize != 4 or not host_out.flags.c_contiguous or host_out.size < total:
+            raise ValueError("host_out must be a contiguous 4-byte array of >= %d elements" % total)
+        ptr = host_out.ctypes.data
+    else:
+        if host_out.is_cuda or host_out.element_size() != 4 or host_out.numel() < total:
+            raise ValueError("host_out must be a CPU tensor of >= %d 4-byte elements" % total)
+        ptr = host_out.data_ptr()
+    _call("mtgp_generate_to_host", streams.handle, _p32(ids), _p64(counts), ids.size, int(fmt),
+          ptr, int(chunk_bytes), _stream_handle(stream))
+
+
+def mtgp_check(streams: Streams, stream=None):
+    _call("mtgp_check", streams.handle, _stream_handle(stream))
+
+
+def mtgp_get_launch_config(streams: Streams) -> dict:
+    c = LaunchConfig()
+    _call("mtgp_get_launch_config", streams.handle, ctypes.byref(c))
+    return c.as_dict()
+
+
+def mtgp_set_launch_config(streams: Streams, warps_per_cta=4, ctas_per_sm=0, words_per_lane=8,
+                           kernel=0):
+    c = LaunchConfig(warps_per_cta, ctas_per_sm, words_per_lane, kernel)
+    _call("mtgp_set_launch_config", streams.handle, ctypes.byref(c))
+
+
+def mtgp_autotune(streams: Streams, fmt=MTGP_U32, sample_streams=0, sample_count=0) -> dict:
+    c = LaunchConfig()
+    _call("mtgp_autotune", streams.handle, int(fmt), sample_streams, sample_count, ctypes.byref(c))
+    return c.as_dict()
+
+
+def mtgp_plan_create(streams: Streams, stream_ids, counts, fmt, out) -> Plan:
+    ids, counts = _req_arrays(stream_ids, counts)
+    total = int(counts.sum()) if counts.size else 0
+    h = _VP()
+    _call("mtgp_plan_create", streams.handle, _p32(ids), _p64(counts), ids.size, int(fmt),
+          _dev_ptr(out, total), ctypes.byref(h))
+    return Plan(h, streams, out)
+
+
+def mtgp_plan_launch(plan: Plan, stream=None):
+    _call("mtgp_plan_launch", plan.handle, _stream_handle(stream))
+
+
+def mtgp_plan_autotune(plan: Plan) -> dict:
+    c = LaunchConfig()
+    _call("mtgp_plan_autotune", plan.handle, ctypes.byref(c))
+    return c.as_dict()
+
+
+def mtgp_plan_get_info(plan: Plan) -> dict:
+    i = PlanInfo()
+    _call("mtgp_plan_get_info", plan.handle, ctypes.byref(i))
+    return {"total_numbers": i.total_numbers, "n_items": i.n_items,
+            "kernel_launches": i.kernel_launches, "config": i.config.as_dict(),
+            "grid_ctas": i.grid_ctas}

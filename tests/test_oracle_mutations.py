@@ -1,0 +1,61 @@
+"""The pins must reject plausible mistakes in the oracle.
+
+Each case copies the oracle's C source, plants one mistake by text
+substitution (a wrong index, shift direction, dropped term, transposed
+operand, ...), compiles the copy, and runs the pin suite against it in a
+subprocess.  The pin suite has to fail for every planted mistake.  CPU only.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mtgp_oracle.c")
+
+MUTANTS = {
+    "successor_index": ("uint32_t y = (x[i] & p->mask) ^ x[i + 1];",
+                        "uint32_t y = (x[i] & p->mask) ^ x[i + 2];"),
+    "pos_index": ("y ^= x[i + p->pos] >> p->sh2;", "y ^= x[i + p->pos + 1] >> p->sh2;"),
+    "sh1_direction": ("y ^= y << p->sh1;", "y ^= y >> p->sh1;"),
+    "sh2_direction": ("y ^= x[i + p->pos] >> p->sh2;", "y ^= x[i + p->pos] << p->sh2;"),
+    "mask_dropped": ("uint32_t y = (x[i] & p->mask) ^ x[i + 1];",
+                     "uint32_t y = x[i] ^ x[i + 1];"),
+    "mask_on_successor": ("uint32_t y = (x[i] & p->mask) ^ x[i + 1];",
+                          "uint32_t y = x[i] ^ (x[i + 1] & p->mask);"),
+    "rec_index_bits": ("x[i + n] = y ^ p->rec_tbl[y & 0xFu];",
+                       "x[i + n] = y ^ p->rec_tbl[(y >> 28) & 0xFu];"),
+    "tempering_word": ("uint32_t t = x[i + p->pos - 1];", "uint32_t t = x[i + p->pos];"),
+    "fold_dropped": ("t ^= t >> 8;\n", "\n"),
+    "temper_pre_table": ("uint32_t o = x[i + n] ^ p->tmp_tbl[t & 0xFu];",
+                         "uint32_t o = y ^ p->tmp_tbl[t & 0xFu];"),
+    "mantissa_shift": ("uint32_t bits12 = 0x3F800000u | (o >> 9);",
+                       "uint32_t bits12 = 0x3F800000u | (o >> 9) | 1u;"),
+    "state_save_offset": ("memcpy(state, x + count, (size_t)n * sizeof(uint32_t));",
+                          "memcpy(state, x + count + 1, (size_t)(n - 1) * sizeof(uint32_t));"),
+    "seed_shift": ("(state[i - 1] ^ (state[i - 1] >> 30)) + i;",
+                   "(state[i - 1] ^ (state[i - 1] >> 29)) + i;"),
+    "table_span": ("if (k & (1u << b))", "if (k & (1u << (3 - b)))"),
+    "mask_width": ("p->mask = 0xFFFFFFFFu << (uint32_t)r;",
+                   "p->mask = 0xFFFFFFFFu << (uint32_t)(r - 1);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_planted_mistake(name, tmp_path):
+    before, after = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(before) == 1, name
+    mutant_c = tmp_path / "mutant.c"
+    mutant_c.write_text(src.replace(before, after))
+    # the header sits beside the original source
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-shared", "-fPIC",
+                           "-I", os.path.join(ROOT, "oracle"), "-o", str(lib), str(mutant_c),
+                           "-lpthread"])
+    env = dict(os.environ, MTGP_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "pins accepted mutant %s:\n%s" % (name, r.stdout[-2000:])
