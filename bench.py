@@ -63,14 +63,14 @@ def recorded_traffic():
     return float(m_b.group(1))
 
 
-def workload(name: str, rank: int):
+def workload(name: str, rank: int, streams: int = 0, count: int = 0):
     if name == "uneven":
         w = workloads.uneven()
         desc = ("uneven: 10000 MTGP32 Mexp 11213 streams, counts floor(2^U), U~U[10,22] "
                 "(seed 7)")
     elif name == "equal":
-        w = workloads.equal()
-        desc = "equal: 4096 MTGP32 Mexp 11213 streams x 2^18"
+        w = workloads.equal(streams or 4096, count or (1 << 18))
+        desc = "equal: %d MTGP32 Mexp 11213 streams x %d" % (streams or 4096, count or (1 << 18))
     elif name.startswith("long"):
         w = workloads.long_streams(int(name[4:]))
         desc = "long: 1024 MTGP32 Mexp %s streams x 2^20" % name[4:]
@@ -131,45 +131,30 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 27, seed=0):
+def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 26, seed=0):
     """Times the CPU oracle on a bounded random sample of the workload's
-    streams (outputs discarded batch by batch).  Returns (numbers/s, numbers,
-    seconds, streams)."""
+    streams: whole streams in random order, in batches of at most max_batch
+    numbers (outputs discarded batch by batch), until budget_s seconds of
+    oracle time have been spent.  Returns (numbers/s, numbers, seconds,
+    streams)."""
     import oracle
     p = oracle.params_generate(w["mexp"], workloads.PARAM_SEED)
-    rng = np.random.default_rng(seed)
-    order = rng.permutation(w["seeds"].size)
-    # calibrate on a small batch
-    cal = order[:max(4, threads)]
-    cal_counts = np.minimum(w["counts"][cal], np.uint64(1 << 16))
-    st = np.stack([oracle.init_state(p, int(w["seeds"][i])) for i in cal])
-    t0 = time.perf_counter()
-    oracle.generate_many(p, st, np.arange(cal.size), cal_counts, 0, threads)
-    rate0 = float(cal_counts.sum()) / max(time.perf_counter() - t0, 1e-6)
-    target = rate0 * budget_s
-    picked, tot = [], 0
-    for i in order:
-        if tot >= target:
-            break
-        picked.append(int(i))
-        tot += int(w["counts"][i])
-    picked = np.array(picked)
-    states = np.stack([oracle.init_state(p, int(w["seeds"][i])) for i in picked])
-    counts = w["counts"][picked]
-    done, t_all = 0, 0.0
-    b0 = 0
-    while b0 < picked.size:
-        b1 = b0
-        acc = 0
-        while b1 < picked.size and (acc == 0 or acc + int(counts[b1]) <= max_batch):
-            acc += int(counts[b1])
-            b1 += 1
+    order = np.random.default_rng(seed).permutation(w["seeds"].size)
+    done, t_all, used, k = 0, 0.0, 0, 0
+    while t_all < budget_s and k < order.size:
+        batch, acc = [], 0
+        while k < order.size and len(batch) < 4 * threads and (
+                acc == 0 or acc + int(w["counts"][order[k]]) <= max_batch):
+            batch.append(int(order[k]))
+            acc += int(w["counts"][order[k]])
+            k += 1
+        states = np.stack([oracle.init_state(p, int(w["seeds"][i])) for i in batch])
         t0 = time.perf_counter()
-        oracle.generate_many(p, states[b0:b1], np.arange(b1 - b0), counts[b0:b1], 0, threads)
+        oracle.generate_many(p, states, np.arange(len(batch)), w["counts"][batch], 0, threads)
         t_all += time.perf_counter() - t0
         done += acc
-        b0 = b1
-    return done / t_all, done, t_all, picked.size
+        used += len(batch)
+    return done / t_all, done, t_all, used
 
 
 def run_reference(args, rank, world):
@@ -213,7 +198,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w, desc = workload(args.workload, rank)
+    w, desc = workload(args.workload, rank, args.streams, args.count)
     counts = w["counts"]
     total = int(counts.sum())
     stream = torch.cuda.Stream()
@@ -305,6 +290,11 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         e2e = measure_e2e(mtgp, torch, st, ids, counts, stream, args)
 
+    serving = None
+    if rank == 0 and args.serving_seconds > 0:
+        del plan
+        serving = measure_serving(mtgp, torch, args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -335,6 +325,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": e2e,
             "gpu_launches": args.steps * info["kernel_launches"],
             "bit_exact_sample": bit_exact,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -373,6 +364,30 @@ def measure_e2e(mtgp, torch, st, ids, counts, stream, args):
             "steps": args.e2e_steps, "api": "mtgp_generate_to_host (pinned host output)"}
 
 
+def measure_serving(mtgp, torch, args):
+    """Continuous batching vs one launch per request on the serving trace."""
+    tr = workloads.serving_trace(duration_s=args.serving_seconds)
+    params = mtgp.mtgp_params_generate(workloads.MEXP_MAIN, workloads.PARAM_SEED)
+    st = mtgp.mtgp_init_statuses(params, np.arange(tr["n_streams"], dtype=np.uint32))
+    srv = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4)
+    res = {"workload": "65536 resident Mexp 11213 streams; Poisson %.0f req/s (seed 11) for %.1f s; "
+                       "k = floor(2^U), U~U[8,20]; u32 or f32[0,1); arena (admission cap) 8 GiB"
+                       % (50000, args.serving_seconds),
+           "requests": int(tr["t"].size),
+           "offered_gnum_s": float(tr["counts"].sum()) / args.serving_seconds / 1e9}
+    for mode, name in [(0, "continuous_batching"), (1, "one_launch_per_request")]:
+        lat, _, stats = mtgp.mtgp_server_run_trace(srv, tr["t"], tr["ids"], tr["counts"], tr["fmt"],
+                                                   mode=mode)
+        res[name] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                     "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                     "mean_ms": 1e3 * float(lat.mean()),
+                     "gnum_s": stats["numbers"] / stats["elapsed"] / 1e9,
+                     "kernel_launches": int(stats["ticks"]), "elapsed_s": stats["elapsed"]}
+    srv.close()
+    st.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,8 +395,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uneven")
+    ap.add_argument("--streams", type=int, default=0, help="equal workload: stream count")
+    ap.add_argument("--count", type=int, default=0, help="equal workload: numbers per stream")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
+                    help="length of the serving trace (0 = skip the serving measurement)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -49,6 +49,7 @@ extern "C" {
 typedef struct mtgp_params*  mtgp_params_t;   /* immutable after creation      */
 typedef struct mtgp_streams* mtgp_streams_t;  /* n_streams device-resident states */
 typedef struct mtgp_plan*    mtgp_plan_t;     /* a recorded batched launch     */
+typedef struct mtgp_server*  mtgp_server_t;   /* continuous-batching front end */
 
 typedef enum {
     MTGP_OK = 0,
@@ -174,12 +175,16 @@ mtgp_status mtgp_streams_free(mtgp_streams_t streams);
 /* ---------------------------------------------------------------------- */
 
 typedef struct {
-    uint32_t warps_per_cta;   /* block size / 32: 1..16                         */
+    uint32_t warps_per_cta;   /* block size / 32: 1..8 (the register-resident
+                                 path uses 2, 4 or 8)                          */
     uint32_t ctas_per_sm;     /* resident CTAs per SM (0 = occupancy maximum)   */
     uint32_t words_per_lane;  /* sub-steps per parallel step (4 or 8); the
                                  window is 32 * words_per_lane <= N - pos      */
     uint32_t kernel;          /* 0 = register-resident path when available,
                                  1 = shared-memory ring path (any parameters)  */
+    uint32_t coop_percent;    /* streams of a launch longer than coop_percent/100
+                                 times the numbers per warp slot are advanced
+                                 by a whole CTA (longest first); 0 = never     */
 } mtgp_launch_config;
 
 mtgp_status mtgp_get_launch_config(mtgp_streams_t streams, mtgp_launch_config* cfg);
@@ -216,6 +221,7 @@ typedef struct {
     uint32_t kernel_launches; /* kernels per plan launch                       */
     mtgp_launch_config config;
     uint32_t grid_ctas;
+    uint32_t n_coop;          /* streams advanced by whole CTAs                 */
 } mtgp_plan_info;
 
 /* Times the tuning candidates on this plan's own work table, on a scratch
@@ -226,6 +232,92 @@ mtgp_status mtgp_plan_autotune(mtgp_plan_t plan, mtgp_launch_config* best);
 
 mtgp_status mtgp_plan_get_info(mtgp_plan_t plan, mtgp_plan_info* info);
 mtgp_status mtgp_plan_free(mtgp_plan_t plan);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching over resident streams                     */
+/* ---------------------------------------------------------------------- */
+/* Clients ask for k numbers of stream s (the per-block streams of Sec. 3.2
+ * consumed by a running simulation).  States stay resident in HBM.  A
+ * request is admitted when its stream is not inside an in-flight tick and
+ * its output fits in the device arena (the admission cap); admitted
+ * requests are coalesced into a tick, one kernel launch; up to max_inflight
+ * ticks run at once on separate CUDA streams.  Requests for one stream
+ * complete in submission order and produce exactly the numbers a lone
+ * request sequence would. */
+
+typedef struct {
+    uint64_t arena_bytes;        /* device output arena = admission cap (0 = 8 GiB) */
+    uint32_t max_inflight;       /* ticks in flight at once, 1..64 (0 = 4)          */
+    uint32_t max_tick_requests;  /* requests coalesced into one tick (0 = 4096)     */
+} mtgp_server_config;
+
+typedef struct {
+    uint64_t tag;                /* the caller's tag from mtgp_server_submit        */
+    uint64_t count;              /* numbers produced                                */
+    uint64_t arena_offset;       /* element offset of the result in the arena       */
+    int32_t  fmt;                /* mtgp_format of the result                       */
+    int32_t  pad;
+    double   submit_time;        /* seconds, steady clock                           */
+    double   done_time;          /* seconds, when completion was observed           */
+} mtgp_completion;
+
+typedef struct {
+    uint64_t requests;           /* completed                                       */
+    uint64_t numbers;            /* produced                                        */
+    uint64_t ticks;              /* kernel launches                                 */
+    double   elapsed;            /* seconds from the first arrival to the last completion */
+    double   busy_wait;          /* seconds the loop idled while requests were queued */
+} mtgp_server_stats;
+
+/* Creates a server over `streams` (kept by reference; must outlive the
+ * server).  The arena is a library-owned device buffer of cfg->arena_bytes
+ * (cfg may be NULL for the defaults). */
+mtgp_status mtgp_server_create(mtgp_streams_t streams, const mtgp_server_config* cfg,
+                               mtgp_server_t* out);
+
+/* Queues a request for `count` numbers of stream `stream_id` in format
+ * `fmt`.  MTGP_EBUSY if count * 4 bytes exceeds the whole arena, MTGP_EINVAL
+ * for a bad id or format. */
+mtgp_status mtgp_server_submit(mtgp_server_t server, uint32_t stream_id, uint64_t count,
+                               mtgp_format fmt, uint64_t tag);
+
+/* Non-blocking: collects finished ticks, then admits queued requests into
+ * one tick and launches it if a tick slot is free.  Up to `max_out`
+ * completions are copied to the host array `out`; *n_out receives their
+ * number (the rest stay queued for later calls).  A completion's result
+ * stays valid in the arena until mtgp_server_release. */
+mtgp_status mtgp_server_progress(mtgp_server_t server, mtgp_completion* out, uint32_t max_out,
+                                 uint32_t* n_out);
+
+/* Returns a completed result's arena space (offset and count as reported). */
+mtgp_status mtgp_server_release(mtgp_server_t server, uint64_t arena_offset, uint64_t count);
+
+/* Device pointer of the arena (4-byte elements). */
+mtgp_status mtgp_server_arena(mtgp_server_t server, void** arena);
+
+/* Copies `count` elements starting at arena element `arena_offset` to the
+ * host array `host_dst` (synchronous; for clients that consume results on
+ * the CPU).  MTGP_EINVAL if the range leaves the arena. */
+mtgp_status mtgp_server_read(mtgp_server_t server, uint64_t arena_offset, uint64_t count,
+                             void* host_dst);
+
+/* Replays an arrival trace in real time on an idle server: request j
+ * arrives t_arrival[j] seconds after the call starts (non-decreasing) and
+ * asks for counts[j] numbers of stream ids[j] in format fmts[j]; latency[j]
+ * receives arrival-to-observed-completion seconds.  All arrays are host
+ * arrays of n entries.  mode 0 = continuous batching (ticks as above);
+ * mode 1 = one launch per request on 16 CUDA streams (stream id mod 16), the
+ * comparison.  If record_offsets is non-NULL it receives each result's
+ * arena offset and no arena space is reused (the arena must then hold the
+ * whole trace).  Synchronous. */
+mtgp_status mtgp_server_run_trace(mtgp_server_t server, const double* t_arrival,
+                                  const uint32_t* ids, const uint64_t* counts,
+                                  const int32_t* fmts, uint32_t n, uint32_t mode,
+                                  double* latency, uint64_t* record_offsets,
+                                  mtgp_server_stats* stats);
+
+/* Waits for in-flight ticks and frees the server and its arena. */
+mtgp_status mtgp_server_free(mtgp_server_t server);
 
 /* ---------------------------------------------------------------------- */
 

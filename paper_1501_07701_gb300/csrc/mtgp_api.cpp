@@ -290,9 +290,10 @@ extern "C" mtgp_status mtgp_params_free(mtgp_params_t params)
 // ---------------------------------------------------------------------------
 mtgp_status mtgp::build_work(uint32_t n_streams, const uint32_t* ids, const uint64_t* counts,
                              const int32_t* fmts, uint32_t fmt_all, uint32_t n_req,
-                             uint64_t out_base, Work& w)
+                             uint64_t out_base, Work& w, const uint64_t* out_offs)
 {
     w.items.clear();
+    w.item_total.clear();
     w.segs.clear();
     w.total = 0;
     w.max_item = 0;
@@ -317,10 +318,11 @@ mtgp_status mtgp::build_work(uint32_t n_streams, const uint32_t* ids, const uint
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t a, uint32_t b) { return ids[a] < ids[b]; });
     // exclusive scan of counts in request order gives the output offsets
+    // (unless the caller places every request itself)
     std::vector<uint64_t> off(n_req);
     uint64_t acc = out_base;
     for (uint32_t j = 0; j < n_req; ++j) {
-        off[j] = acc;
+        off[j] = out_offs ? out_offs[j] : acc;
         acc += counts[j];
     }
     size_t i = 0;
@@ -358,8 +360,11 @@ mtgp_status mtgp::build_work(uint32_t n_streams, const uint32_t* ids, const uint
         idx[k] = (uint32_t)k;
     std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return tot[a] > tot[b]; });
     std::vector<WorkItem> sorted(w.items.size());
-    for (size_t k = 0; k < idx.size(); ++k)
+    w.item_total.resize(w.items.size());
+    for (size_t k = 0; k < idx.size(); ++k) {
         sorted[k] = w.items[idx[k]];
+        w.item_total[k] = tot[idx[k]];
+    }
     w.items.swap(sorted);
     w.total = total;
     return MTGP_OK;
@@ -405,7 +410,7 @@ DeviceGuard::~DeviceGuard()
         cudaSetDevice(prev);
 }
 
-static void free_slot(TableSlot& s)
+void mtgp::free_table_slot(TableSlot& s)
 {
     if (s.ev_recorded)
         cudaEventSynchronize(s.ev);
@@ -425,7 +430,7 @@ static void destroy_streams(mtgp_streams* h)
         return;
     DeviceGuard g(h->device);
     for (auto& s : h->slots) {
-        free_slot(s);
+        free_table_slot(s);
         if (s.ev)
             cudaEventDestroy(s.ev);
     }
@@ -512,9 +517,22 @@ LaunchCfg mtgp::default_config(const KParams& P)
     c.ctas_per_sm = 0;
     c.k = 8;
     c.kernel = 0;
+    c.coop_percent = 100;
     if (!fast_supported(P, 8))
         c.k = fast_supported(P, 4) ? 4 : 8;
     return c;
+}
+
+uint32_t mtgp::coop_count(const Work& w, const Geometry& g, int coop_percent)
+{
+    if (g.kernel != 0 || coop_percent <= 0 || w.items.empty())
+        return 0;
+    const double slots = (double)g.grid * (double)(g.threads / 32);
+    const double thr = (double)w.total / slots * (double)coop_percent / 100.0;
+    uint32_t n = 0;
+    while (n < w.item_total.size() && (double)w.item_total[n] >= thr)
+        ++n;
+    return n;
 }
 
 extern "C" mtgp_status mtgp_streams_info(mtgp_streams_t st, uint32_t* n_streams, uint32_t* n_words)
@@ -588,6 +606,16 @@ mtgp_status mtgp::launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& 
         return MTGP_OK;
     TableSlot& sl = st->slots[st->next_slot];
     st->next_slot = (st->next_slot + 1) % (int)st->slots.size();
+    return launch_work_slot(st, sl, w, cfg, out, s);
+}
+
+// Uploads a work table through `sl` (waiting for the slot's previous
+// consumer) and launches on `s`; records the slot's event after the kernel.
+mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w,
+                                   const LaunchCfg& cfg, void* out, cudaStream_t s)
+{
+    if (w.items.empty())
+        return MTGP_OK;
     if (sl.ev_recorded) {
         CUDA_TRY(cudaEventSynchronize(sl.ev), "cudaEventSynchronize(table slot)");
         sl.ev_recorded = false;
@@ -621,6 +649,7 @@ mtgp_status mtgp::launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& 
     a.items = (const WorkItem*)((char*)sl.dev + io);
     a.segs = (const Segment*)((char*)sl.dev + so);
     a.n_items = (uint32_t)w.items.size();
+    a.n_coop = coop_count(w, g, cfg.coop_percent);
     a.counter = (uint32_t*)sl.dev;
     a.out = (uint32_t*)out;
     a.err = st->d_err;
@@ -799,6 +828,7 @@ static mtgp_launch_config to_public(const LaunchCfg& c)
     o.ctas_per_sm = (uint32_t)c.ctas_per_sm;
     o.words_per_lane = (uint32_t)c.k;
     o.kernel = (uint32_t)c.kernel;
+    o.coop_percent = (uint32_t)c.coop_percent;
     return o;
 }
 
@@ -822,10 +852,13 @@ mtgp_status mtgp::validate_config(const mtgp_launch_config* c, LaunchCfg* out)
         return fail(MTGP_EINVAL, "kernel %u not 0 or 1", c->kernel);
     if (c->ctas_per_sm > 64)
         return fail(MTGP_EINVAL, "ctas_per_sm %u", c->ctas_per_sm);
+    if (c->coop_percent > 100000)
+        return fail(MTGP_EINVAL, "coop_percent %u", c->coop_percent);
     out->warps_per_cta = (int)c->warps_per_cta;
     out->ctas_per_sm = (int)c->ctas_per_sm;
     out->k = (int)c->words_per_lane;
     out->kernel = (int)c->kernel;
+    out->coop_percent = (int)c->coop_percent;
     return MTGP_OK;
 }
 
@@ -844,26 +877,30 @@ extern "C" mtgp_status mtgp_set_launch_config(mtgp_streams_t st, const mtgp_laun
 std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
 {
     std::vector<LaunchCfg> v;
-    for (int k : {8, 4}) {
-        if (!fast_supported(P, k))
-            continue;
-        for (int w : {2, 4, 8})
-            for (int c : {0, 4}) {
+    for (int k : {8, 4})
+        for (int w : {2, 4, 8}) {
+            if (!fast_supported(P, k, w))
+                continue;
+            for (int coop : {0, 50, 100, 200}) {
                 LaunchCfg x;
                 x.warps_per_cta = w;
-                x.ctas_per_sm = c == 0 ? 0 : (c * 4) / w;   // half-occupancy variant
+                x.ctas_per_sm = 0;
                 x.k = k;
                 x.kernel = 0;
+                x.coop_percent = coop;
                 v.push_back(x);
             }
-    }
-    for (int w : {4, 8}) {
-        LaunchCfg x;
-        x.warps_per_cta = w;
-        x.ctas_per_sm = 0;
-        x.k = 8;
-        x.kernel = 1;
-        v.push_back(x);
+        }
+    if (v.empty()) {   // no register-resident instantiation: tune the ring kernel
+        for (int w : {2, 4, 8}) {
+            LaunchCfg x;
+            x.warps_per_cta = w;
+            x.ctas_per_sm = 0;
+            x.k = 8;
+            x.kernel = 1;
+            x.coop_percent = 0;
+            v.push_back(x);
+        }
     }
     return v;
 }
@@ -1007,7 +1044,7 @@ static mtgp_status record_graph(mtgp_plan* p)
         return MTGP_OK;
     cudaStream_t cap = p->cap_stream;
     CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    cudaError_t e1 = cudaMemsetAsync(p->d_table, 0, sizeof(uint32_t), cap);
+    cudaError_t e1 = cudaMemsetAsync(p->d_table, 0, 2 * sizeof(uint32_t), cap);
     GenArgs a;
     a.P = p->st->P.k;
     a.states = p->st->d_states;
@@ -1015,6 +1052,8 @@ static mtgp_status record_graph(mtgp_plan* p)
     a.items = (const WorkItem*)((char*)p->d_table + p->items_off);
     a.segs = (const Segment*)((char*)p->d_table + p->segs_off);
     a.n_items = p->n_items;
+    a.n_coop = coop_count(p->work, p->geo, p->cfg.coop_percent);
+    p->n_coop = a.n_coop;
     a.counter = (uint32_t*)p->d_table;
     a.out = (uint32_t*)p->out;
     a.err = p->st->d_err;
@@ -1176,6 +1215,7 @@ extern "C" mtgp_status mtgp_plan_get_info(mtgp_plan_t p, mtgp_plan_info* info)
     eff.k = p->geo.k;
     info->config = to_public(eff);
     info->grid_ctas = (uint32_t)p->geo.grid;
+    info->n_coop = p->n_coop;
     return ok();
 }
 

@@ -1,32 +1,36 @@
 // Register-resident MTGP32 generation kernel for sm_103a.
 //
-// One warp advances one stream at a time (the paper's "PRNG per block of
-// threads", Sec. 2, with the state in on-chip storage while it is advanced
-// and in global memory between launches).  Layout of a stream's state while
-// it is on chip:
+// Streams are advanced by one warp each (the paper's "PRNG per block of
+// threads", Sec. 2, with the state on chip while it is advanced and in global
+// memory between launches), or -- for the longest streams of a launch -- by
+// all G warps of a CTA together.
 //
+// Layout of a stream's state while it is on chip:
 //   * The sequence is cut into rows of N words: column c of row q holds
 //     x_{qN + c}.  Computing row q+1 column c needs (row q, c) and
 //     (row q, c+1) [the words i and i+1 of the recurrence] and the word i+pos,
 //     which is (row q, c+pos) when c+pos < N and (row q+1, c+pos-N) otherwise;
-//     the tempering word i+pos-1 likewise.  So at every moment a state needs
-//     only the latest value of each column.
-//   * Lane l of the warp keeps columns 32m + l, m = 0..M-1 (M = ceil(N/32)),
-//     in registers r[m]: word i is the lane's own register and word i+1 is
-//     one shuffle away.
-//   * The latest value of every column is also published in a per-warp
-//     shared-memory array S[0..N) (plus a mirror S[N..N+32) of columns 0..31
-//     and a guard S[-1] of column N-1), from which the words i+pos and
-//     i+pos-1 are read for 32 consecutive columns at once without a modulo.
+//     the tempering word i+pos-1 likewise.  So a state needs only the latest
+//     value of each column.
+//   * Column group m (columns 32m .. 32m+31) belongs to one warp; lane l of
+//     that warp keeps column 32m + l in a register (word i).
+//   * The latest value of every column is also published in a shared-memory
+//     row S[0..N), with a mirror S[N..N+32) of columns 0..31 and a guard
+//     S[-1] of column N-1.  Words i+1, i+pos and i+pos-1 of 32 consecutive
+//     columns are then plain conflict-free loads at S[c+1], S[c+pos],
+//     S[c+pos-1] with no modulo (the mirror supplies the wrapped columns).
 //   * The recursion and tempering tables live in lane registers (lane l holds
 //     entry l & 15); a lookup is one shuffle whose source lane is the index
 //     itself (shfl uses the low five bits of the lane operand).
+//   * Shifts are done as integer multiplies (x << s = x * 2^s and x >> s =
+//     high word of x * 2^(32-s)), which run on the FMA pipe and leave the ALU
+//     pipe to the XORs.
 //
-// A sub-step m computes columns 32m..32m+31 of the next row (one new word
-// per lane).  K consecutive sub-steps form one parallel step of 32K words:
-// all of them read only words produced before the step when 32K <= N - pos
-// (the block-parallel window of the method), so the step reads everything,
-// then writes everything, with one warp barrier in between.
+// A sub-step m computes columns 32m..32m+31 of the next row (one new word per
+// lane).  K consecutive sub-steps form one parallel step of 32K words; when
+// 32K <= N - pos none of them reads a word produced in the same step (the
+// block-parallel window of the method), so a step reads everything, passes a
+// barrier, then writes everything.
 #pragma once
 
 #include "mtgp_internal.h"
@@ -47,6 +51,37 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Multipliers for the shifts (sh1, sh2 in 1..31): y << sh1 = y * m1,
+// x >> sh2 = umulhi(x, m2).
+struct Shifts {
+    uint32_t m1, m2;
+};
+
+__device__ __forceinline__ Shifts make_shifts(const KParams& P)
+{
+    Shifts s;
+    s.m1 = 1u << P.sh1;
+    s.m2 = 1u << (32u - P.sh2);
+    return s;
+}
+
+// The new word of one column from words i (own register), i+1, i+pos.
+__device__ __forceinline__ uint32_t recur(uint32_t xi, uint32_t x1, uint32_t xp, uint32_t mask,
+                                          const Shifts& sh, uint32_t tR)
+{
+    uint32_t y = (xi & mask) ^ x1;
+    y = y ^ (y * sh.m1) ^ __umulhi(xp, sh.m2);
+    return y ^ __shfl_sync(MTGP_FULL, tR, y);
+}
+
+// Tempering index from word i+pos-1: fold >> 16 then >> 8 (low four bits
+// are used; the shuffle ignores bit 4 because the tables repeat).
+__device__ __forceinline__ uint32_t temper_index(uint32_t xq)
+{
+    const uint32_t t = xq ^ __umulhi(xq, 1u << 16);
+    return t ^ __umulhi(t, 1u << 24);
+}
+
 // Output conversion from the new word v and the tempering index ti.
 //   FMT 0: v ^ TMP[ti]
 //   FMT 1: (v >> 9) ^ FLT[ti]   == 0x3F800000 | ((v ^ TMP[ti]) >> 9)
@@ -56,161 +91,232 @@ __device__ __forceinline__ uint32_t temper_convert(uint32_t v, uint32_t ti, uint
 {
     if (FMT == 0)
         return v ^ __shfl_sync(MTGP_FULL, tT, ti);
-    const uint32_t b = (v >> 9) ^ __shfl_sync(MTGP_FULL, tF, ti);
+    const uint32_t b = __umulhi(v, 1u << 23) ^ __shfl_sync(MTGP_FULL, tF, ti);
     if (FMT == 1)
         return b;
     return __float_as_uint(__uint_as_float(b) - 1.0f);
 }
 
-// Pick-up offset of sub-step m: (pos + 32m) mod N (pos < N and 32m < N).
-__device__ __forceinline__ uint32_t pick_offset(uint32_t pos, uint32_t n, int m)
+// Per-lane output of the slow path: the lane finds its request and format.
+__device__ __forceinline__ void slow_store(uint32_t v, uint32_t ti, uint32_t tT, uint32_t tF,
+                                           uint64_t g, const Segment* __restrict__ segs,
+                                           uint32_t s_first, uint32_t s_end, uint32_t* __restrict__ out)
 {
-    const uint32_t sp = pos + 32u * (uint32_t)m;
-    return sp >= n ? sp - n : sp;
+    const uint32_t ou = temper_convert<0>(v, ti, tT, tF);
+    const uint32_t of = temper_convert<1>(v, ti, tT, tF);
+    uint32_t s = s_first;
+    while (s + 1 < s_end && g >= segs[s + 1].g_start)
+        ++s;
+    const Segment sg = segs[s];
+    uint32_t o = ou;
+    if (sg.fmt == 1)
+        o = of;
+    else if (sg.fmt == 2)
+        o = __float_as_uint(__uint_as_float(of) - 1.0f);
+    out[sg.out_off + (g - sg.g_start)] = o;
 }
 
-// One full row (N new words) inside a single request: output goes to
-// orow[0..N).
-template <int M, int K, int FMT>
-__device__ __forceinline__ void fast_row(uint32_t (&r)[M], uint32_t* __restrict__ S,
-                                         uint32_t* __restrict__ orow, const KParams& P,
-                                         uint32_t lane, uint32_t tR, uint32_t tT, uint32_t tF,
-                                         uint32_t src_last, uint32_t last_lane)
+// ===========================================================================
+// Rows.  A row is "full" when all N of its words go to one request; other
+// rows (the last, partial row of a stream, or a row crossing requests) take
+// the slow path where each lane finds its own request.
+//
+// Work split: sub-step m of a row belongs to warp (m mod WG) of the WG warps
+// advancing the stream (WG = 1 for a warp-owned stream); that warp keeps
+// columns 32m + lane in register r[m / WG].  `Sw` = S + 32*warp + lane.
+// ===========================================================================
+template <int M, int K, int WG, int FMT, bool SLOW>
+__device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32_t* __restrict__ S,
+                                        uint32_t* __restrict__ Sw, uint32_t* __restrict__ ow,
+                                        const KParams& P, const Shifts& sh, uint32_t warp,
+                                        uint32_t lane, uint32_t tR, uint32_t tT, uint32_t tF,
+                                        uint32_t last_lane, uint32_t n_valid, uint64_t row_g,
+                                        const Segment* __restrict__ segs, uint32_t s_first,
+                                        uint32_t s_end, uint32_t* __restrict__ out)
 {
-    const uint32_t src_next = (lane + 1) & 31u;
+    constexpr int J = (M + WG - 1) / WG;
+    constexpr int PER = K / WG;   // sub-steps per warp in one parallel step
 #pragma unroll
-    for (int m0 = 0; m0 < M; m0 += K) {
-        uint32_t xn[K], ov[K];
-#pragma unroll
-        for (int t = 0; t < K; ++t) {
-            const int m = m0 + t;
-            if (m < M) {
-                // word i+1: column 32m+l+1 -> lane l+1, or lane 0's next
-                // register for l = 31; the row's last column takes the new
-                // column 0 (lane 0's r[0], already advanced).
-                const uint32_t nb = (lane == 0) ? r[(m + 1 < M) ? m + 1 : 0] : r[m];
-                const uint32_t x1 = __shfl_sync(MTGP_FULL, nb, (m + 1 < M) ? src_next : src_last);
-                const uint32_t* q = S + pick_offset(P.pos, P.n, m) + lane;
-                const uint32_t xp = q[0];    // word i+pos
-                const uint32_t xq = q[-1];   // word i+pos-1
-                uint32_t y = (r[m] & P.mask) ^ x1;
-                y ^= (y << P.sh1) ^ (xp >> P.sh2);
-                const uint32_t v = y ^ __shfl_sync(MTGP_FULL, tR, y);
-                uint32_t ti = xq ^ (xq >> 16);
-                ti ^= ti >> 8;
-                xn[t] = v;
-                ov[t] = temper_convert<FMT>(v, ti, tT, tF);
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < K; ++t) {
-            const int m = m0 + t;
-            if (m < M) {
-                if (m < M - 1 || lane <= last_lane) {
-                    r[m] = xn[t];
-                    S[32 * m + lane] = xn[t];
-                    __stcs(orow + 32 * m + lane, ov[t]);
-                }
-                if (m == 0)
-                    S[P.n + lane] = xn[t];
-                if (m == M - 1 && lane == last_lane)
-                    S[-1] = xn[t];
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// A row that is partial (n_valid < N columns) or crosses request
-// boundaries: every lane finds its own request and format.
-template <int M, int K>
-__device__ __forceinline__ void slow_row(uint32_t (&r)[M], uint32_t* __restrict__ S, const KParams& P,
-                                      uint32_t lane, uint32_t tR, uint32_t tT, uint32_t tF,
-                                      uint32_t src_last, uint32_t last_lane, uint32_t n_valid,
-                                      uint64_t row_g, const Segment* __restrict__ segs,
-                                      uint32_t s_first, uint32_t s_end, uint32_t* __restrict__ out)
-{
-    const uint32_t src_next = (lane + 1) & 31u;
-#pragma unroll
-    for (int m0 = 0; m0 < M; m0 += K) {
-        if (32u * (uint32_t)m0 >= n_valid)
+    for (int s0 = 0; s0 < M; s0 += K) {
+        if (SLOW && 32u * (uint32_t)s0 >= n_valid)
             break;
-        uint32_t xn[K], ou[K], of[K];
+        uint32_t xn[PER], ti[PER];
 #pragma unroll
-        for (int t = 0; t < K; ++t) {
-            const int m = m0 + t;
-            if (m < M) {
-                const uint32_t nb = (lane == 0) ? r[(m + 1 < M) ? m + 1 : 0] : r[m];
-                const uint32_t x1 = __shfl_sync(MTGP_FULL, nb, (m + 1 < M) ? src_next : src_last);
-                const uint32_t* q = S + pick_offset(P.pos, P.n, m) + lane;
-                const uint32_t xp = q[0];
-                const uint32_t xq = q[-1];
-                uint32_t y = (r[m] & P.mask) ^ x1;
-                y ^= (y << P.sh1) ^ (xp >> P.sh2);
-                const uint32_t v = y ^ __shfl_sync(MTGP_FULL, tR, y);
-                uint32_t ti = xq ^ (xq >> 16);
-                ti ^= ti >> 8;
-                xn[t] = v;
-                ou[t] = temper_convert<0>(v, ti, tT, tF);
-                of[t] = temper_convert<1>(v, ti, tT, tF);
+        for (int i = 0; i < PER; ++i) {
+            const int j = s0 / WG + i;
+            const uint32_t m = (uint32_t)(s0 + i * WG) + (WG > 1 ? warp : 0u);
+            if (j < J && m < (uint32_t)M) {
+                const int off = 32 * (s0 + i * WG);            // static part of 32m
+                uint32_t sp = P.pos + 32u * m;                  // (pos + 32m) mod N
+                sp = sp >= P.n ? sp - P.n : sp;
+                const uint32_t* q = S + sp + lane;
+                xn[i] = recur(r[j], Sw[off + 1], q[0], P.mask, sh, tR);
+                ti[i] = temper_index(q[-1]);
             }
         }
-        __syncwarp();
+        if (WG > 1)
+            __syncthreads();
+        else
+            __syncwarp();
 #pragma unroll
-        for (int t = 0; t < K; ++t) {
-            const int m = m0 + t;
-            if (m < M) {
-                const uint32_t col = 32u * (uint32_t)m + lane;
-                if (col < n_valid) {   // n_valid <= N, so col is a real column
-                    r[m] = xn[t];
-                    S[col] = xn[t];
+        for (int i = 0; i < PER; ++i) {
+            const int j = s0 / WG + i;
+            const uint32_t m = (uint32_t)(s0 + i * WG) + (WG > 1 ? warp : 0u);
+            if (j < J && m < (uint32_t)M) {
+                const int off = 32 * (s0 + i * WG);
+                const uint32_t col = 32u * m + lane;
+                const bool act = SLOW ? (col < n_valid) : (m + 1u < (uint32_t)M || lane <= last_lane);
+                if (act) {
+                    r[j] = xn[i];
+                    Sw[off] = xn[i];
                     if (m == 0)
-                        S[P.n + lane] = xn[t];
-                    if (col == P.n - 1)
-                        S[-1] = xn[t];
-                    const uint64_t g = row_g + col;
-                    uint32_t s = s_first;
-                    while (s + 1 < s_end && g >= segs[s + 1].g_start)
-                        ++s;
-                    const Segment sg = segs[s];
-                    uint32_t o = ou[t];
-                    if (sg.fmt == 1)
-                        o = of[t];
-                    else if (sg.fmt == 2)
-                        o = __float_as_uint(__uint_as_float(of[t]) - 1.0f);
-                    out[sg.out_off + (g - sg.g_start)] = o;
+                        S[P.n + lane] = xn[i];
+                    if (col == P.n - 1u)
+                        S[-1] = xn[i];
+                    if (SLOW)
+                        slow_store(xn[i], ti[i], tT, tF, row_g + col, segs, s_first, s_end, out);
+                    else
+                        __stcs(ow + off, temper_convert<FMT>(xn[i], ti[i], tT, tF));
                 }
             }
         }
-        __syncwarp();
+        if (WG > 1)
+            __syncthreads();
+        else
+            __syncwarp();
     }
-    (void)last_lane;
 }
 
-template <int M, int K>
-__global__ void __launch_bounds__(256) mtgp_fast_kernel(const KParams P, uint32_t* __restrict__ states,
-                                                        uint32_t n_streams,
-                                                        const WorkItem* __restrict__ items,
-                                                        const Segment* __restrict__ segs,
-                                                        uint32_t n_items, uint32_t* __restrict__ counter,
-                                                        uint32_t* __restrict__ out, int* __restrict__ err)
+// Advances one stream by the segments [s_begin, s_end) of the work table.
+// WG warps take part (WG = 1: this warp alone; WG = G: the whole CTA).
+template <int M, int K, int WG>
+__device__ __forceinline__ void run_item(const KParams& P, uint32_t* __restrict__ g, uint32_t* __restrict__ S,
+                                         const Segment* __restrict__ segs, uint32_t s_begin,
+                                         uint32_t s_end, uint32_t* __restrict__ out, uint32_t warp,
+                                         uint32_t lane, uint32_t tR, uint32_t tT, uint32_t tF)
+{
+    constexpr int J = (M + WG - 1) / WG;
+    const uint32_t N = P.n;
+    const uint32_t tid = WG > 1 ? threadIdx.x : lane;
+    const uint32_t wk = WG > 1 ? warp : 0u;
+    const Shifts sh = make_shifts(P);
+    const uint32_t last_lane = (N - 1u) & 31u;   // lane of column N-1 (group M-1)
+
+    // stage in: the state row (HBM) -> S through 16-byte cp.async
+    for (uint32_t c = tid; c < (P.np >> 2); c += 32u * WG)
+        cp_async16(S + 4u * c, g + 4u * c);
+    cp_async_wait_all();
+    if (WG > 1)
+        __syncthreads();
+    else
+        __syncwarp();
+    uint32_t r[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint32_t c = 32u * (wk + (uint32_t)(j * WG)) + lane;
+        r[j] = c < N ? S[c] : 0u;
+    }
+    const uint32_t mirror = S[lane];
+    const uint32_t guard = S[N - 1u];
+    if (WG > 1)
+        __syncthreads();
+    else
+        __syncwarp();
+    if (wk == 0) {
+        S[N + lane] = mirror;
+        if (lane == 0)
+            S[-1] = guard;
+    }
+    if (WG > 1)
+        __syncthreads();
+    else
+        __syncwarp();
+
+    uint32_t* Sw = S + 32u * wk + lane;
+    const Segment last = segs[s_end - 1u];
+    const uint64_t total = last.g_start + last.count;
+    uint32_t s = s_begin;
+    for (uint64_t row = 0; row < total; row += N) {
+        while (segs[s].g_start + segs[s].count <= row)
+            ++s;
+        const Segment sg = segs[s];
+        const uint64_t left = total - row;
+        const uint32_t n_valid = left < (uint64_t)N ? (uint32_t)left : N;
+        if (n_valid == N && row + N <= sg.g_start + sg.count) {
+            uint32_t* ow = out + sg.out_off + (row - sg.g_start) + 32u * wk + lane;
+            if (sg.fmt == 0)
+                gen_row<M, K, WG, 0, false>(r, S, Sw, ow, P, sh, wk, lane, tR, tT, tF, last_lane, N, row,
+                                            segs, s, s_end, out);
+            else if (sg.fmt == 1)
+                gen_row<M, K, WG, 1, false>(r, S, Sw, ow, P, sh, wk, lane, tR, tT, tF, last_lane, N, row,
+                                            segs, s, s_end, out);
+            else
+                gen_row<M, K, WG, 2, false>(r, S, Sw, ow, P, sh, wk, lane, tR, tT, tF, last_lane, N, row,
+                                            segs, s, s_end, out);
+        } else {
+            gen_row<M, K, WG, 0, true>(r, S, Sw, nullptr, P, sh, wk, lane, tR, tT, tF, last_lane, n_valid,
+                                       row, segs, s, s_end, out);
+        }
+    }
+
+    // stage out: oldest word first, x_total .. x_{total+N-1}; the column of
+    // x_{total+j} is (total + j) mod N
+    const uint32_t phase = (uint32_t)(total % N);
+    for (uint32_t j = tid; j < N; j += 32u * WG) {
+        uint32_t c = phase + j;
+        c = c >= N ? c - N : c;
+        g[j] = S[c];
+    }
+    if (WG > 1)
+        __syncthreads();
+    else
+        __syncwarp();
+}
+
+// Persistent kernel.  Phase 1: the CTA claims the longest streams (items
+// [0, n_coop) of the table, sorted longest first) one at a time and its G
+// warps advance each together.  Phase 2: every warp claims the remaining
+// items [n_coop, n_items) one by one and advances each alone.
+template <int M, int K, int G>
+__global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint32_t* __restrict__ states,
+                                                           uint32_t n_streams,
+                                                           const WorkItem* __restrict__ items,
+                                                           const Segment* __restrict__ segs,
+                                                           uint32_t n_items, uint32_t n_coop,
+                                                           uint32_t* __restrict__ counters,
+                                                           uint32_t* __restrict__ out, int* __restrict__ err)
 {
     extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ uint32_t s_claim;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t N = P.n;
-    uint32_t* S = smem + warp * fast_smem_words(N) + 4;
     const uint32_t tR = P.rec[lane & 15u];
     const uint32_t tT = P.tmp[lane & 15u];
     const uint32_t tF = P.flt[lane & 15u];
-    const uint32_t last_lane = (N - 1u) & 31u;   // lane of column N-1 in sub-step M-1
-    const uint32_t src_last = (lane == last_lane) ? 0u : ((lane + 1u) & 31u);
 
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_claim = atomicAdd(&counters[0], 1u);
+        __syncthreads();
+        const uint32_t it = s_claim;
+        __syncthreads();
+        if (it >= n_coop)
+            break;
+        const WorkItem w = items[it];
+        if (w.stream >= n_streams || w.nseg == 0) {
+            if (threadIdx.x == 0)
+                atomicOr(err, 1);
+            continue;
+        }
+        run_item<M, K, G>(P, states + (size_t)w.stream * P.np, smem + 4, segs, w.seg_begin,
+                          w.seg_begin + w.nseg, out, warp, lane, tR, tT, tF);
+    }
+
+    uint32_t* S = smem + warp * fast_smem_words(P.n) + 4;
     for (;;) {
         uint32_t it = 0;
         if (lane == 0)
-            it = atomicAdd(counter, 1u);
+            it = n_coop + atomicAdd(&counters[1], 1u);
         it = __shfl_sync(MTGP_FULL, it, 0);
         if (it >= n_items)
             break;
@@ -220,60 +326,8 @@ __global__ void __launch_bounds__(256) mtgp_fast_kernel(const KParams P, uint32_
                 atomicOr(err, 1);
             continue;
         }
-        uint32_t* g = states + (size_t)w.stream * P.np;
-
-        // Stage in: the N-word state row (HBM) -> S, 16-byte cp.async chunks.
-        for (uint32_t c = lane; c < (P.np >> 2); c += 32u)
-            cp_async16(S + 4u * c, g + 4u * c);
-        cp_async_wait_all();
-        __syncwarp();
-        uint32_t r[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const uint32_t c = 32u * (uint32_t)m + lane;
-            r[m] = c < N ? S[c] : 0u;
-        }
-        const uint32_t mirror = S[lane];
-        const uint32_t guard = S[N - 1u];
-        __syncwarp();
-        S[N + lane] = mirror;
-        if (lane == 0)
-            S[-1] = guard;
-        __syncwarp();
-
-        const uint32_t s_end = w.seg_begin + w.nseg;
-        const Segment last = segs[s_end - 1u];
-        const uint64_t total = last.g_start + last.count;
-        uint32_t s = w.seg_begin;
-        for (uint64_t row = 0; row < total; row += N) {
-            while (segs[s].g_start + segs[s].count <= row)
-                ++s;
-            const Segment sg = segs[s];
-            const uint64_t left = total - row;
-            const uint32_t n_valid = left < (uint64_t)N ? (uint32_t)left : N;
-            if (n_valid == N && row + N <= sg.g_start + sg.count) {
-                uint32_t* orow = out + sg.out_off + (row - sg.g_start);
-                if (sg.fmt == 0)
-                    fast_row<M, K, 0>(r, S, orow, P, lane, tR, tT, tF, src_last, last_lane);
-                else if (sg.fmt == 1)
-                    fast_row<M, K, 1>(r, S, orow, P, lane, tR, tT, tF, src_last, last_lane);
-                else
-                    fast_row<M, K, 2>(r, S, orow, P, lane, tR, tT, tF, src_last, last_lane);
-            } else {
-                slow_row<M, K>(r, S, P, lane, tR, tT, tF, src_last, last_lane, n_valid, row, segs, s,
-                               s_end, out);
-            }
-        }
-
-        // Stage out: oldest word first, x_total .. x_{total+N-1}; column of
-        // x_{total+j} is (total + j) mod N.
-        const uint32_t phase = (uint32_t)(total % N);
-        for (uint32_t j = lane; j < N; j += 32u) {
-            uint32_t c = phase + j;
-            c = c >= N ? c - N : c;
-            g[j] = S[c];
-        }
-        __syncwarp();
+        run_item<M, K, 1>(P, states + (size_t)w.stream * P.np, S, segs, w.seg_begin,
+                          w.seg_begin + w.nseg, out, warp, lane, tR, tT, tF);
     }
 }
 

@@ -42,10 +42,12 @@ struct Segment {
 };
 
 struct LaunchCfg {
-    int warps_per_cta;   // 1..8
+    int warps_per_cta;   // G: 2, 4 or 8 for the register-resident kernel (1..8 ring)
     int ctas_per_sm;     // 0 = occupancy maximum
     int k;               // sub-steps per parallel step (words per lane), 4 or 8
     int kernel;          // 0 register-resident, 1 shared-memory ring
+    int coop_percent;    // streams longer than coop_percent/100 x (numbers per warp
+                         // slot) are advanced by a whole CTA; 0 = never
 };
 
 // Per-warp shared-memory footprint (32-bit words).
@@ -55,9 +57,10 @@ struct LaunchCfg {
 __host__ __device__ inline uint32_t fast_smem_words(uint32_t n) { return 4u + ((n + 32u + 3u) & ~3u); }
 __host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return (n + 3u) & ~3u; }
 
-// True if the register-resident kernel has an instantiation for this N and
-// the window 32*k fits: 32*k <= N - pos.
-bool fast_supported(const KParams& P, int k);
+// True if the register-resident kernel has an instantiation for this N, k
+// and g warps per CTA, the window 32*k fits (32*k <= N - pos), and the
+// shifts are in 1..31.
+bool fast_supported(const KParams& P, int k, int g = 4);
 
 // Seed status -> state rows (row stride P.np words; padding words zeroed).
 cudaError_t launch_init(const KParams& P, const uint32_t* d_seeds, uint32_t n_streams,
@@ -70,7 +73,8 @@ struct GenArgs {
     const WorkItem* items;
     const Segment* segs;
     uint32_t n_items;
-    uint32_t* counter;   // zeroed before the launch
+    uint32_t n_coop;     // items [0, n_coop) are advanced by whole CTAs
+    uint32_t* counter;   // two claim counters, zeroed before the launch
     uint32_t* out;
     int* err;
 };
@@ -96,8 +100,8 @@ cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
 // Fast-kernel launchers, one translation unit per group of state sizes.
 // M = ceil(N / 32) register columns per lane; returns cudaErrorInvalidValue
 // if M or K has no instantiation.
-cudaError_t launch_fast(int M, int K, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
+cudaError_t launch_fast(int M, int K, int G, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
                         cudaStream_t s);
-const void* fast_kernel_ptr(int M, int K);
+const void* fast_kernel_ptr(int M, int K, int G);
 
 }  // namespace mtgp

@@ -164,16 +164,18 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
 // ---------------------------------------------------------------------------
 static int fast_m(const KParams& P) { return (int)((P.n + 31u) / 32u); }
 
-bool fast_supported(const KParams& P, int k)
+bool fast_supported(const KParams& P, int k, int g)
 {
     if (k != 4 && k != 8)
         return false;
     if (P.n < 64 || 32u * (uint32_t)k > P.n - P.pos)
         return false;
+    if (P.sh1 < 1 || P.sh1 > 31 || P.sh2 < 1 || P.sh2 > 31)
+        return false;
     const int M = fast_m(P);
     if (M <= k)
         return false;
-    return fast_kernel_ptr(M, k) != nullptr;
+    return fast_kernel_ptr(M, k, g) != nullptr;
 }
 
 cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_items, int device,
@@ -181,20 +183,26 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
 {
     int k = cfg.k;
     int kernel = cfg.kernel;
-    if (kernel == 0 && !fast_supported(P, k)) {
-        if (k == 8 && fast_supported(P, 4))
-            k = 4;
-        else
-            kernel = 1;
+    int warps = std::max(1, std::min(8, cfg.warps_per_cta));
+    if (kernel == 0) {
+        // register-resident kernel: G in {2, 4, 8} (8 only with k = 8)
+        warps = warps <= 2 ? 2 : (warps <= 4 ? 4 : 8);
+        if (!fast_supported(P, k, warps)) {
+            if (fast_supported(P, 4, std::min(warps, 4))) {
+                k = 4;
+                warps = std::min(warps, 4);
+            } else {
+                kernel = 1;
+            }
+        }
     }
-    const int warps = std::max(1, std::min(8, cfg.warps_per_cta));
     g->kernel = kernel;
     g->k = k;
     g->threads = warps * 32;
     const void* fn;
     if (kernel == 0) {
         g->smem = (size_t)warps * fast_smem_words(P.n) * 4u;
-        fn = fast_kernel_ptr(fast_m(P), k);
+        fn = fast_kernel_ptr(fast_m(P), k, warps);
     } else {
         g->smem = (size_t)(32u + warps * ring_smem_words(P.n)) * 4u;
         fn = (const void*)mtgp_ring_kernel;
@@ -228,7 +236,8 @@ cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
     if (a.n_items == 0)
         return cudaSuccess;
     if (g.kernel == 0)
-        return launch_fast((int)((a.P.n + 31u) / 32u), g.k, a, dim3(g.grid), dim3(g.threads), g.smem, s);
+        return launch_fast((int)((a.P.n + 31u) / 32u), g.k, g.threads / 32, a, dim3(g.grid),
+                           dim3(g.threads), g.smem, s);
     mtgp_ring_kernel<<<g.grid, g.threads, g.smem, s>>>(a.P, a.states, a.n_streams, a.items, a.segs,
                                                        a.n_items, a.counter, a.out, a.err);
     return cudaGetLastError();
@@ -238,24 +247,24 @@ cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
 
 namespace mtgp {
 
-const void* fast_ptr_group_a(int M, int K);
-const void* fast_ptr_group_b(int M, int K);
-const void* fast_ptr_group_c(int M, int K);
+const void* fast_ptr_group_a(int M, int K, int G);
+const void* fast_ptr_group_b(int M, int K, int G);
+const void* fast_ptr_group_c(int M, int K, int G);
 
-const void* fast_kernel_ptr(int M, int K)
+const void* fast_kernel_ptr(int M, int K, int G)
 {
-    const void* p = fast_ptr_group_a(M, K);
+    const void* p = fast_ptr_group_a(M, K, G);
     if (!p)
-        p = fast_ptr_group_b(M, K);
+        p = fast_ptr_group_b(M, K, G);
     if (!p)
-        p = fast_ptr_group_c(M, K);
+        p = fast_ptr_group_c(M, K, G);
     return p;
 }
 
-cudaError_t launch_fast(int M, int K, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
+cudaError_t launch_fast(int M, int K, int G, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
                         cudaStream_t s)
 {
-    const void* fn = fast_kernel_ptr(M, K);
+    const void* fn = fast_kernel_ptr(M, K, G);
     if (!fn)
         return cudaErrorInvalidValue;
     KParams P = a.P;
@@ -264,10 +273,11 @@ cudaError_t launch_fast(int M, int K, const GenArgs& a, dim3 grid, dim3 block, s
     const WorkItem* items = a.items;
     const Segment* segs = a.segs;
     uint32_t n_items = a.n_items;
+    uint32_t n_coop = a.n_coop;
     uint32_t* counter = a.counter;
     uint32_t* out = a.out;
     int* err = a.err;
-    void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &counter, &out, &err};
+    void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &n_coop, &counter, &out, &err};
     return cudaLaunchKernel(fn, grid, block, args, smem, s);
 }
 

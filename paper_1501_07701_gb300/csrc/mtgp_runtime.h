@@ -22,6 +22,7 @@ namespace mtgp {
 // count, longest first.
 struct Work {
     std::vector<WorkItem> items;
+    std::vector<uint64_t> item_total;   // numbers per item, same order as items
     std::vector<Segment> segs;
     uint64_t total = 0;
     uint64_t max_item = 0;
@@ -78,6 +79,7 @@ struct mtgp_plan {
     mtgp_streams* st = nullptr;
     void* out = nullptr;
     uint32_t n_items = 0;
+    uint32_t n_coop = 0;
     uint64_t total = 0;
     uint64_t max_item = 0;
     mtgp::LaunchCfg cfg{};
@@ -93,16 +95,24 @@ struct mtgp_plan {
 
 namespace mtgp {
 
+// Groups requests per stream (request order kept), sorts streams longest
+// first.  Request j's output goes to out_offs[j] if out_offs is given, else
+// to out_base + the exclusive prefix sum of counts.
 mtgp_status build_work(uint32_t n_streams, const uint32_t* ids, const uint64_t* counts,
                        const int32_t* fmts, uint32_t fmt_all, uint32_t n_req, uint64_t out_base,
-                       Work& w);
+                       Work& w, const uint64_t* out_offs = nullptr);
 size_t table_bytes(const Work& w, size_t* items_off, size_t* segs_off);
 void fill_table(const Work& w, void* host);
 LaunchCfg default_config(const KParams& P);
 mtgp_status geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t n_items, Geometry* g);
 mtgp_status launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
                         cudaStream_t s);
+mtgp_status launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w, const LaunchCfg& cfg,
+                             void* out, cudaStream_t s);
+void free_table_slot(TableSlot& s);
 mtgp_status validate_config(const mtgp_launch_config* c, LaunchCfg* out);
+// Number of leading (longest) items a launch hands to whole CTAs.
+uint32_t coop_count(const Work& w, const Geometry& g, int coop_percent);
 std::vector<LaunchCfg> tuning_candidates(const KParams& P);
 mtgp_status time_config(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, uint32_t* states,
                         void* out, int reps, float* best_ms);

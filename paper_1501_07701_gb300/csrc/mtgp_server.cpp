@@ -1,0 +1,598 @@
+// Serving front end: requests "k numbers from stream s" against resident
+// stream states, admitted by output-arena space, coalesced into ticks (one
+// kernel launch each) that overlap on the device on separate CUDA streams.
+//
+// Ordering: a stream whose request is inside an in-flight tick is busy; its
+// later requests wait (and block every request behind them for the same
+// stream) until that tick completes, so each stream sees its requests in
+// submission order and no two kernels touch one state at once.  Requests for
+// one stream admitted into the same tick become consecutive segments of one
+// work item, in order.
+#include <time.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <thread>
+#include <vector>
+
+#include "mtgp_runtime.h"
+
+using namespace mtgp;
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over the arena, in 32-element (128-byte) granules.
+struct ArenaAlloc {
+    std::map<uint64_t, uint64_t> free_;   // offset -> size (elements)
+    uint64_t total = 0;
+    uint64_t used = 0;
+
+    void reset(uint64_t elems)
+    {
+        free_.clear();
+        total = elems & ~31ull;
+        used = 0;
+        if (total)
+            free_[0] = total;
+    }
+    static uint64_t round(uint64_t n) { return (std::max<uint64_t>(n, 1) + 31) & ~31ull; }
+    bool alloc(uint64_t n, uint64_t* off)
+    {
+        n = round(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const uint64_t rest = it->second - n;
+                const uint64_t noff = it->first + n;
+                free_.erase(it);
+                if (rest)
+                    free_[noff] = rest;
+                used += n;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t n)
+    {
+        n = round(n);
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct Req {
+    uint32_t stream;
+    int32_t fmt;
+    uint64_t count;
+    uint64_t tag;
+    uint64_t off;        // arena element offset once admitted
+    double t_submit;
+    bool live;
+};
+
+struct Tick {
+    std::vector<uint32_t> reqs;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    TableSlot slot;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct mtgp_server {
+    mtgp_streams* st = nullptr;
+    mtgp_server_config cfg{};
+    void* arena = nullptr;
+    ArenaAlloc alloc;
+    std::vector<Req> reqs;
+    std::vector<uint32_t> free_reqs;
+    std::list<uint32_t> pending;
+    std::vector<uint8_t> busy;          // per stream: inside an in-flight tick
+    std::vector<uint32_t> blocked;      // per stream: epoch stamp of the current admission scan
+    uint32_t epoch = 0;
+    std::vector<Tick> ticks;
+    std::deque<mtgp_completion> done;
+    uint64_t n_ticks = 0;
+    uint64_t n_numbers = 0;
+    uint64_t n_requests = 0;
+    bool keep_results = false;          // trace mode with recorded offsets
+};
+
+static void destroy_server(mtgp_server* s)
+{
+    if (!s)
+        return;
+    DeviceGuard g(s->st->device);
+    for (Tick& t : s->ticks) {
+        if (t.cs)
+            cudaStreamSynchronize(t.cs);
+        free_table_slot(t.slot);
+        if (t.slot.ev)
+            cudaEventDestroy(t.slot.ev);
+        if (t.ev)
+            cudaEventDestroy(t.ev);
+        if (t.cs)
+            cudaStreamDestroy(t.cs);
+    }
+    if (s->arena)
+        cudaFree(s->arena);
+    delete s;
+}
+
+extern "C" mtgp_status mtgp_server_create(mtgp_streams_t st, const mtgp_server_config* cfg,
+                                          mtgp_server_t* out)
+{
+    try {
+        if (!st || !out)
+            return fail(MTGP_EINVAL, "null argument");
+        mtgp_server_config c{};
+        if (cfg)
+            c = *cfg;
+        if (c.arena_bytes == 0)
+            c.arena_bytes = 8ull << 30;
+        if (c.max_inflight == 0)
+            c.max_inflight = 4;
+        if (c.max_tick_requests == 0)
+            c.max_tick_requests = 4096;
+        if (c.max_inflight > 64)
+            return fail(MTGP_EINVAL, "max_inflight %u > 64", c.max_inflight);
+        DeviceGuard g(st->device);
+        mtgp_server* s = new mtgp_server;
+        s->st = st;
+        s->cfg = c;
+        s->busy.assign(st->n_streams, 0);
+        s->blocked.assign(st->n_streams, 0);
+        s->ticks.resize(c.max_inflight);
+        cudaError_t e = cudaMalloc(&s->arena, c.arena_bytes);
+        if (e != cudaSuccess) {
+            destroy_server(s);
+            return fail_cuda(e, "cudaMalloc(arena)");
+        }
+        s->alloc.reset(c.arena_bytes / 4);
+        for (Tick& t : s->ticks) {
+            if ((e = cudaStreamCreateWithFlags(&t.cs, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&t.slot.ev, cudaEventDisableTiming)) != cudaSuccess) {
+                destroy_server(s);
+                return fail_cuda(e, "server stream/event");
+            }
+        }
+        *out = s;
+        return ok();
+    } catch (...) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+static uint32_t new_req(mtgp_server* s)
+{
+    if (!s->free_reqs.empty()) {
+        const uint32_t i = s->free_reqs.back();
+        s->free_reqs.pop_back();
+        return i;
+    }
+    s->reqs.push_back(Req{});
+    return (uint32_t)s->reqs.size() - 1;
+}
+
+static mtgp_status submit(mtgp_server* s, uint32_t stream, uint64_t count, int32_t fmt, uint64_t tag,
+                          double t_submit)
+{
+    if (stream >= s->st->n_streams)
+        return fail(MTGP_EINVAL, "stream id %u >= %u", stream, s->st->n_streams);
+    if (fmt < 0 || fmt > 2)
+        return fail(MTGP_EINVAL, "format %d", fmt);
+    if (count == 0 || ArenaAlloc::round(count) > s->alloc.total)
+        return fail(MTGP_EBUSY, "request of %llu numbers cannot fit the arena (%llu elements)",
+                    (unsigned long long)count, (unsigned long long)s->alloc.total);
+    const uint32_t i = new_req(s);
+    Req& r = s->reqs[i];
+    r.stream = stream;
+    r.fmt = fmt;
+    r.count = count;
+    r.tag = tag;
+    r.off = 0;
+    r.t_submit = t_submit;
+    r.live = true;
+    s->pending.push_back(i);
+    return MTGP_OK;
+}
+
+extern "C" mtgp_status mtgp_server_submit(mtgp_server_t s, uint32_t stream_id, uint64_t count,
+                                          mtgp_format fmt, uint64_t tag)
+{
+    if (!s)
+        return fail(MTGP_EINVAL, "null server");
+    try {
+        mtgp_status r = submit(s, stream_id, count, (int32_t)fmt, tag, now_s());
+        return r == MTGP_OK ? ok() : r;
+    } catch (...) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+// Collects finished ticks.  Completed requests go to s->done.
+static mtgp_status reap(mtgp_server* s, int* n_reaped)
+{
+    *n_reaped = 0;
+    for (Tick& t : s->ticks) {
+        if (!t.busy)
+            continue;
+        const cudaError_t e = cudaEventQuery(t.ev);
+        if (e == cudaErrorNotReady)
+            continue;
+        if (e != cudaSuccess)
+            return fail_cuda(e, "tick completion");
+        const double tn = now_s();
+        for (uint32_t i : t.reqs) {
+            Req& r = s->reqs[i];
+            mtgp_completion c;
+            c.tag = r.tag;
+            c.count = r.count;
+            c.arena_offset = r.off;
+            c.fmt = r.fmt;
+            c.pad = 0;
+            c.submit_time = r.t_submit;
+            c.done_time = tn;
+            s->done.push_back(c);
+            s->busy[r.stream] = 0;
+            r.live = false;
+            s->free_reqs.push_back(i);
+            s->n_numbers += r.count;
+            ++s->n_requests;
+        }
+        t.reqs.clear();
+        t.busy = false;
+        ++*n_reaped;
+    }
+    return MTGP_OK;
+}
+
+// Admits pending requests into one free tick slot and launches it.  Sets
+// *launched to 1 if a tick went out.
+static mtgp_status admit_and_launch(mtgp_server* s, int* launched)
+{
+    *launched = 0;
+    if (s->pending.empty())
+        return MTGP_OK;
+    Tick* t = nullptr;
+    for (Tick& x : s->ticks)
+        if (!x.busy) {
+            t = &x;
+            break;
+        }
+    if (!t)
+        return MTGP_OK;
+    ++s->epoch;
+    if (s->epoch == 0) {
+        std::fill(s->blocked.begin(), s->blocked.end(), 0);
+        s->epoch = 1;
+    }
+    std::vector<uint32_t> ids;
+    std::vector<uint64_t> counts, offs;
+    std::vector<int32_t> fmts;
+    for (auto it = s->pending.begin(); it != s->pending.end();) {
+        Req& r = s->reqs[*it];
+        if (s->busy[r.stream] || s->blocked[r.stream] == s->epoch) {
+            s->blocked[r.stream] = s->epoch;   // keeps this stream's later requests behind it
+            ++it;
+            continue;
+        }
+        if (t->reqs.size() >= s->cfg.max_tick_requests)
+            break;
+        uint64_t off;
+        if (!s->alloc.alloc(r.count, &off))
+            break;   // arena full: first come, first served
+        r.off = off;
+        t->reqs.push_back(*it);
+        ids.push_back(r.stream);
+        counts.push_back(r.count);
+        offs.push_back(off);
+        fmts.push_back(r.fmt);
+        it = s->pending.erase(it);
+    }
+    if (t->reqs.empty())
+        return MTGP_OK;
+    for (uint32_t i : t->reqs)
+        s->busy[s->reqs[i].stream] = 1;
+    Work w;
+    mtgp_status st = build_work(s->st->n_streams, ids.data(), counts.data(), fmts.data(), 0,
+                                (uint32_t)ids.size(), 0, w, offs.data());
+    if (st != MTGP_OK)
+        return st;
+    st = launch_work_slot(s->st, t->slot, w, s->st->cfg, s->arena, t->cs);
+    if (st != MTGP_OK)
+        return st;
+    cudaError_t e = cudaEventRecord(t->ev, t->cs);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "cudaEventRecord(tick)");
+    t->busy = true;
+    ++s->n_ticks;
+    *launched = 1;
+    return MTGP_OK;
+}
+
+extern "C" mtgp_status mtgp_server_progress(mtgp_server_t s, mtgp_completion* out, uint32_t max_out,
+                                            uint32_t* n_out)
+{
+    if (!s || (max_out && !out))
+        return fail(MTGP_EINVAL, "null argument");
+    try {
+        DeviceGuard g(s->st->device);
+        int n = 0;
+        mtgp_status st = reap(s, &n);
+        if (st != MTGP_OK)
+            return st;
+        st = admit_and_launch(s, &n);
+        if (st != MTGP_OK)
+            return st;
+        uint32_t k = 0;
+        while (k < max_out && !s->done.empty()) {
+            out[k++] = s->done.front();
+            s->done.pop_front();
+        }
+        if (n_out)
+            *n_out = k;
+        return ok();
+    } catch (...) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+extern "C" mtgp_status mtgp_server_release(mtgp_server_t s, uint64_t arena_offset, uint64_t count)
+{
+    if (!s)
+        return fail(MTGP_EINVAL, "null server");
+    s->alloc.release(arena_offset, count);
+    return ok();
+}
+
+extern "C" mtgp_status mtgp_server_arena(mtgp_server_t s, void** arena)
+{
+    if (!s || !arena)
+        return fail(MTGP_EINVAL, "null argument");
+    *arena = s->arena;
+    return ok();
+}
+
+extern "C" mtgp_status mtgp_server_read(mtgp_server_t s, uint64_t arena_offset, uint64_t count,
+                                        void* host_dst)
+{
+    if (!s || (count && !host_dst))
+        return fail(MTGP_EINVAL, "null argument");
+    if (arena_offset > s->cfg.arena_bytes / 4 || count > s->cfg.arena_bytes / 4 - arena_offset)
+        return fail(MTGP_EINVAL, "range [%llu, +%llu) leaves the arena", (unsigned long long)arena_offset,
+                    (unsigned long long)count);
+    DeviceGuard g(s->st->device);
+    const cudaError_t e = cudaMemcpy(host_dst, (uint32_t*)s->arena + arena_offset, count * 4,
+                                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "cudaMemcpy(server read)");
+    return ok();
+}
+
+// Short pause for the polling loop: yields, and sleeps when the next event
+// is far away.
+static void pause_until(double t_next)
+{
+    const double dt = t_next - now_s();
+    if (dt > 200e-6)
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    else
+        std::this_thread::yield();
+}
+
+// One launch per request (the comparison): request i goes to CUDA stream
+// lanes[ids[i] % L], so one stream's requests stay in order.
+static mtgp_status run_per_request(mtgp_server* s, const double* t_arr, const uint32_t* ids,
+                                   const uint64_t* counts, const int32_t* fmts, uint32_t n,
+                                   double* latency, uint64_t* rec_offs, double t0)
+{
+    const int L = 16;
+    std::vector<cudaStream_t> lanes(L, nullptr);
+    const size_t NS = 256;
+    std::vector<TableSlot> slots(NS);
+    std::vector<cudaEvent_t> evs(NS, nullptr);
+    std::vector<int64_t> slot_req(NS, -1);
+    mtgp_status rc = MTGP_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < L && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&lanes[i], cudaStreamNonBlocking);
+    for (size_t i = 0; i < NS && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&slots[i].ev, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess)
+        rc = fail_cuda(e, "per-request streams/events");
+    std::vector<uint64_t> offs(n, 0);
+    std::deque<uint32_t> waiting;   // arrived, not launched (arena full)
+    uint32_t next = 0, finished = 0;
+    size_t slot_next = 0;
+    uint32_t in_flight = 0;
+    while (rc == MTGP_OK && finished < n) {
+        const double tnow = now_s() - t0;
+        while (next < n && t_arr[next] <= tnow)
+            waiting.push_back(next++);
+        bool progressed = false;
+        // completions
+        for (size_t k = 0; k < NS && in_flight; ++k) {
+            if (slot_req[k] < 0)
+                continue;
+            e = cudaEventQuery(evs[k]);
+            if (e == cudaErrorNotReady)
+                continue;
+            if (e != cudaSuccess) {
+                rc = fail_cuda(e, "per-request completion");
+                break;
+            }
+            const uint32_t j = (uint32_t)slot_req[k];
+            latency[j] = now_s() - t0 - t_arr[j];
+            if (!rec_offs)
+                s->alloc.release(offs[j], counts[j]);
+            slot_req[k] = -1;
+            --in_flight;
+            ++finished;
+            s->n_numbers += counts[j];
+            ++s->n_requests;
+            progressed = true;
+        }
+        // launches, in arrival order
+        while (rc == MTGP_OK && !waiting.empty() && slot_req[slot_next] < 0) {
+            const uint32_t j = waiting.front();
+            uint64_t off;
+            if (!s->alloc.alloc(counts[j], &off))
+                break;
+            offs[j] = off;
+            if (rec_offs)
+                rec_offs[j] = off;
+            Work w;
+            rc = build_work(s->st->n_streams, &ids[j], &counts[j], &fmts[j], 0, 1, 0, w, &off);
+            if (rc != MTGP_OK)
+                break;
+            cudaStream_t cs = lanes[ids[j] % L];
+            rc = launch_work_slot(s->st, slots[slot_next], w, s->st->cfg, s->arena, cs);
+            if (rc != MTGP_OK)
+                break;
+            if ((e = cudaEventRecord(evs[slot_next], cs)) != cudaSuccess) {
+                rc = fail_cuda(e, "cudaEventRecord");
+                break;
+            }
+            slot_req[slot_next] = j;
+            slot_next = (slot_next + 1) % NS;
+            ++in_flight;
+            ++s->n_ticks;
+            waiting.pop_front();
+            progressed = true;
+        }
+        if (!progressed)
+            pause_until(next < n ? t0 + t_arr[next] : now_s() + 1e-4);
+    }
+    for (int i = 0; i < L; ++i)
+        if (lanes[i]) {
+            cudaStreamSynchronize(lanes[i]);
+            cudaStreamDestroy(lanes[i]);
+        }
+    for (size_t i = 0; i < NS; ++i) {
+        free_table_slot(slots[i]);
+        if (slots[i].ev)
+            cudaEventDestroy(slots[i].ev);
+        if (evs[i])
+            cudaEventDestroy(evs[i]);
+    }
+    return rc;
+}
+
+extern "C" mtgp_status mtgp_server_run_trace(mtgp_server_t s, const double* t_arrival,
+                                             const uint32_t* ids, const uint64_t* counts,
+                                             const int32_t* fmts, uint32_t n, uint32_t mode,
+                                             double* latency, uint64_t* record_offsets,
+                                             mtgp_server_stats* stats)
+{
+    if (!s || (n && (!t_arrival || !ids || !counts || !fmts || !latency)))
+        return fail(MTGP_EINVAL, "null argument");
+    if (mode > 1)
+        return fail(MTGP_EINVAL, "mode %u", mode);
+    try {
+        DeviceGuard g(s->st->device);
+        for (uint32_t j = 0; j < n; ++j) {
+            if (ids[j] >= s->st->n_streams || fmts[j] < 0 || fmts[j] > 2 || counts[j] == 0 ||
+                ArenaAlloc::round(counts[j]) > s->alloc.total)
+                return fail(MTGP_EINVAL, "trace entry %u invalid", j);
+            if (j && t_arrival[j] < t_arrival[j - 1])
+                return fail(MTGP_EINVAL, "arrival times must not decrease (entry %u)", j);
+        }
+        if (!s->pending.empty())
+            return fail(MTGP_EBUSY, "server has pending requests");
+        for (const Tick& t : s->ticks)
+            if (t.busy)
+                return fail(MTGP_EBUSY, "server has ticks in flight");
+        const uint64_t ticks0 = s->n_ticks, nums0 = s->n_numbers, reqs0 = s->n_requests;
+        double busy_wait = 0;
+        const double t0 = now_s();
+        mtgp_status rc = MTGP_OK;
+        if (mode == 1) {
+            rc = run_per_request(s, t_arrival, ids, counts, fmts, n, latency, record_offsets, t0);
+        } else {
+            s->keep_results = record_offsets != nullptr;
+            uint32_t next = 0, finished = 0;
+            std::vector<mtgp_completion> batch;
+            while (finished < n) {
+                const double tnow = now_s() - t0;
+                while (next < n && t_arrival[next] <= tnow) {
+                    rc = submit(s, ids[next], counts[next], fmts[next], next, t0 + t_arrival[next]);
+                    if (rc != MTGP_OK)
+                        break;
+                    ++next;
+                }
+                if (rc != MTGP_OK)
+                    break;
+                int reaped = 0, launched = 0;
+                if ((rc = reap(s, &reaped)) != MTGP_OK)
+                    break;
+                while (!s->done.empty()) {
+                    const mtgp_completion c = s->done.front();
+                    s->done.pop_front();
+                    latency[c.tag] = c.done_time - c.submit_time;
+                    if (record_offsets)
+                        record_offsets[c.tag] = c.arena_offset;
+                    else
+                        s->alloc.release(c.arena_offset, c.count);
+                    ++finished;
+                }
+                if ((rc = admit_and_launch(s, &launched)) != MTGP_OK)
+                    break;
+                if (!reaped && !launched) {
+                    const double tw = now_s();
+                    pause_until(next < n ? t0 + t_arrival[next] : tw + 1e-4);
+                    if (!s->pending.empty())
+                        busy_wait += now_s() - tw;
+                }
+            }
+            s->keep_results = false;
+        }
+        const double t1 = now_s();
+        if (stats) {
+            stats->requests = s->n_requests - reqs0;
+            stats->numbers = s->n_numbers - nums0;
+            stats->ticks = s->n_ticks - ticks0;
+            stats->elapsed = t1 - t0 - (n ? t_arrival[0] : 0);
+            stats->busy_wait = busy_wait;
+        }
+        if (rc != MTGP_OK)
+            return rc;
+        return ok();
+    } catch (...) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+extern "C" mtgp_status mtgp_server_free(mtgp_server_t s)
+{
+    destroy_server(s);
+    return ok();
+}

@@ -40,7 +40,8 @@ class ParamsDesc(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("words_per_lane", ctypes.c_uint32), ("kernel", ctypes.c_uint32)]
+                ("words_per_lane", ctypes.c_uint32), ("kernel", ctypes.c_uint32),
+                ("coop_percent", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -49,7 +50,24 @@ class LaunchConfig(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("total_numbers", ctypes.c_uint64), ("n_items", ctypes.c_uint32),
                 ("kernel_launches", ctypes.c_uint32), ("config", LaunchConfig),
-                ("grid_ctas", ctypes.c_uint32)]
+                ("grid_ctas", ctypes.c_uint32), ("n_coop", ctypes.c_uint32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_tick_requests", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("arena_offset", ctypes.c_uint64), ("fmt", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("submit_time", ctypes.c_double), ("done_time", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("numbers", ctypes.c_uint64),
+                ("ticks", ctypes.c_uint64), ("elapsed", ctypes.c_double),
+                ("busy_wait", ctypes.c_double)]
 
 
 _VP = ctypes.c_void_p
@@ -83,6 +101,16 @@ _SIGS = {
     "mtgp_plan_autotune": [_VP, ctypes.POINTER(LaunchConfig)],
     "mtgp_plan_get_info": [_VP, ctypes.POINTER(PlanInfo)],
     "mtgp_plan_free": [_VP],
+    "mtgp_server_create": [_VP, ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)],
+    "mtgp_server_submit": [_VP, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64],
+    "mtgp_server_progress": [_VP, ctypes.POINTER(Completion), ctypes.c_uint32, _U32P],
+    "mtgp_server_release": [_VP, ctypes.c_uint64, ctypes.c_uint64],
+    "mtgp_server_arena": [_VP, ctypes.POINTER(_VP)],
+    "mtgp_server_read": [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP],
+    "mtgp_server_run_trace": [_VP, ctypes.POINTER(ctypes.c_double), _U32P, _U64P,
+                              ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_uint32,
+                              ctypes.POINTER(ctypes.c_double), _U64P, ctypes.POINTER(ServerStats)],
+    "mtgp_server_free": [_VP],
     "mtgp_last_error": [],
     "mtgp_version": [],
 }
@@ -323,8 +351,8 @@ def mtgp_get_launch_config(streams: Streams) -> dict:
 
 
 def mtgp_set_launch_config(streams: Streams, warps_per_cta=4, ctas_per_sm=0, words_per_lane=8,
-                           kernel=0):
-    c = LaunchConfig(warps_per_cta, ctas_per_sm, words_per_lane, kernel)
+                           kernel=0, coop_percent=100):
+    c = LaunchConfig(warps_per_cta, ctas_per_sm, words_per_lane, kernel, coop_percent)
     _call("mtgp_set_launch_config", streams.handle, ctypes.byref(c))
 
 
@@ -358,4 +386,81 @@ def mtgp_plan_get_info(plan: Plan) -> dict:
     _call("mtgp_plan_get_info", plan.handle, ctypes.byref(i))
     return {"total_numbers": i.total_numbers, "n_items": i.n_items,
             "kernel_launches": i.kernel_launches, "config": i.config.as_dict(),
-            "grid_ctas": i.grid_ctas}
+            "grid_ctas": i.grid_ctas, "n_coop": i.n_coop}
+
+
+class Server:
+    """Owning wrapper of an mtgp_server_t (keeps its Streams alive)."""
+
+    def __init__(self, handle, streams):
+        self.handle = handle
+        self.streams = streams
+
+    def close(self):
+        if self.handle:
+            _call("mtgp_server_free", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mtgp_server_create(streams: Streams, arena_bytes=0, max_inflight=0, max_tick_requests=0):
+    c = ServerConfig(arena_bytes, max_inflight, max_tick_requests)
+    h = _VP()
+    _call("mtgp_server_create", streams.handle, ctypes.byref(c), ctypes.byref(h))
+    return Server(h, streams)
+
+
+def mtgp_server_submit(server: Server, stream_id, count, fmt, tag):
+    _call("mtgp_server_submit", server.handle, int(stream_id), int(count), int(fmt), int(tag))
+
+
+def mtgp_server_progress(server: Server, max_out=1024):
+    """Returns a list of completion dicts."""
+    buf = (Completion * max_out)()
+    n = ctypes.c_uint32()
+    _call("mtgp_server_progress", server.handle, buf, max_out, ctypes.byref(n))
+    return [{"tag": c.tag, "count": c.count, "arena_offset": c.arena_offset, "fmt": c.fmt,
+             "submit_time": c.submit_time, "done_time": c.done_time} for c in buf[:n.value]]
+
+
+def mtgp_server_release(server: Server, arena_offset, count):
+    _call("mtgp_server_release", server.handle, int(arena_offset), int(count))
+
+
+def mtgp_server_arena(server: Server) -> int:
+    h = _VP()
+    _call("mtgp_server_arena", server.handle, ctypes.byref(h))
+    return h.value
+
+
+def mtgp_server_read(server: Server, arena_offset, count) -> np.ndarray:
+    """Copies a result out of the arena (uint32 bit patterns)."""
+    out = np.zeros(max(int(count), 1), np.uint32)
+    _call("mtgp_server_read", server.handle, int(arena_offset), int(count), out.ctypes.data)
+    return out[:int(count)]
+
+
+def mtgp_server_run_trace(server: Server, t_arrival, ids, counts, fmts, mode=0, record=False):
+    """Returns (latency seconds array, arena offsets or None, stats dict)."""
+    t = np.ascontiguousarray(t_arrival, dtype=np.float64)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    fmts = np.ascontiguousarray(fmts, dtype=np.int32)
+    n = t.size
+    if not (ids.size == counts.size == fmts.size == n):
+        raise ValueError("trace arrays must have equal length")
+    lat = np.zeros(n, np.float64)
+    offs = np.zeros(n, np.uint64) if record else None
+    st = ServerStats()
+    _call("mtgp_server_run_trace", server.handle,
+          t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _p32(ids), _p64(counts),
+          fmts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n, int(mode),
+          lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+          _p64(offs) if record else None, ctypes.byref(st))
+    return lat, offs, {"requests": st.requests, "numbers": st.numbers, "ticks": st.ticks,
+                       "elapsed": st.elapsed, "busy_wait": st.busy_wait}
