@@ -32,6 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1501_07701_gb300 import dist as mdist  # noqa: E402
 from paper_1501_07701_gb300 import workloads  # noqa: E402
 
 METRIC = "Gnumbers/s and % of HBM-write roofline, bit-exact; serving p50/p99 latency"
@@ -76,8 +77,7 @@ def workload(name: str, rank: int, streams: int = 0, count: int = 0):
         desc = "long: 1024 MTGP32 Mexp %s streams x 2^20" % name[4:]
     else:
         raise SystemExit("unknown workload " + name)
-    n = w["seeds"].size
-    w["seeds"] = (w["seeds"].astype(np.uint64) + np.uint64(rank * n)).astype(np.uint32)
+    w["seeds"] = mdist.weak_seeds(w["seeds"], rank)
     return w, desc
 
 
@@ -253,10 +253,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     elapsed = t0.elapsed_time(t1) / 1e3
     kern_ms = [a.elapsed_time(b) for a, b in ev]
-    if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = mdist.max_over_ranks(elapsed, device=dev)
     numbers_all = total * args.steps * world
     value = numbers_all / elapsed / 1e9
 

@@ -98,12 +98,12 @@ __device__ __forceinline__ uint32_t temper_convert(uint32_t v, uint32_t ti, uint
 }
 
 // Per-lane output of the slow path: the lane finds its request and format.
-__device__ __forceinline__ void slow_store(uint32_t v, uint32_t ti, uint32_t tT, uint32_t tF,
-                                           uint64_t g, const Segment* __restrict__ segs,
-                                           uint32_t s_first, uint32_t s_end, uint32_t* __restrict__ out)
+// ou / of are the u32 and [1,2) outputs, both computed while the warp was
+// converged (they need shuffles); this function itself is lane-local.
+__device__ __forceinline__ void slow_store(uint32_t ou, uint32_t of, uint64_t g,
+                                           const Segment* __restrict__ segs, uint32_t s_first,
+                                           uint32_t s_end, uint32_t* __restrict__ out)
 {
-    const uint32_t ou = temper_convert<0>(v, ti, tT, tF);
-    const uint32_t of = temper_convert<1>(v, ti, tT, tF);
     uint32_t s = s_first;
     while (s + 1 < s_end && g >= segs[s + 1].g_start)
         ++s;
@@ -124,6 +124,10 @@ __device__ __forceinline__ void slow_store(uint32_t v, uint32_t ti, uint32_t tT,
 // Work split: sub-step m of a row belongs to warp (m mod WG) of the WG warps
 // advancing the stream (WG = 1 for a warp-owned stream); that warp keeps
 // columns 32m + lane in register r[m / WG].  `Sw` = S + 32*warp + lane.
+//
+// Every shuffle (table lookups) runs in the read phase, under conditions that
+// are uniform across the warp; the write phase is lane-predicated and holds
+// no warp-synchronous instruction.
 // ===========================================================================
 template <int M, int K, int WG, int FMT, bool SLOW>
 __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32_t* __restrict__ S,
@@ -140,18 +144,24 @@ __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32
     for (int s0 = 0; s0 < M; s0 += K) {
         if (SLOW && 32u * (uint32_t)s0 >= n_valid)
             break;
-        uint32_t xn[PER], ti[PER];
+        uint32_t xn[PER], o1[PER], o2[PER];
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int j = s0 / WG + i;
             const uint32_t m = (uint32_t)(s0 + i * WG) + (WG > 1 ? warp : 0u);
-            if (j < J && m < (uint32_t)M) {
+            if (j < J && m < (uint32_t)M) {   // uniform across the warp
                 const int off = 32 * (s0 + i * WG);            // static part of 32m
                 uint32_t sp = P.pos + 32u * m;                  // (pos + 32m) mod N
                 sp = sp >= P.n ? sp - P.n : sp;
                 const uint32_t* q = S + sp + lane;
                 xn[i] = recur(r[j], Sw[off + 1], q[0], P.mask, sh, tR);
-                ti[i] = temper_index(q[-1]);
+                const uint32_t ti = temper_index(q[-1]);
+                if (SLOW) {
+                    o1[i] = temper_convert<0>(xn[i], ti, tT, tF);
+                    o2[i] = temper_convert<1>(xn[i], ti, tT, tF);
+                } else {
+                    o1[i] = temper_convert<FMT>(xn[i], ti, tT, tF);
+                }
             }
         }
         if (WG > 1)
@@ -174,9 +184,9 @@ __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32
                     if (col == P.n - 1u)
                         S[-1] = xn[i];
                     if (SLOW)
-                        slow_store(xn[i], ti[i], tT, tF, row_g + col, segs, s_first, s_end, out);
+                        slow_store(o1[i], o2[i], row_g + col, segs, s_first, s_end, out);
                     else
-                        __stcs(ow + off, temper_convert<FMT>(xn[i], ti[i], tT, tF));
+                        __stcs(ow + off, o1[i]);
                 }
             }
         }
