@@ -163,6 +163,25 @@ mtgp_status mtgp_generate_to_host(mtgp_streams_t streams, const uint32_t* stream
                                   const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
                                   void* host_out, uint64_t chunk_bytes, void* cuda_stream);
 
+/* No counterpart in the paper: a variant of mtgp_generate_u32/_f32 for
+ * callers that cannot have device memory allocated on their behalf once
+ * running (a simulation that reserved the GPU's memory up front, a real-time
+ * loop that must not enter the allocator, a host runtime that forbids hidden
+ * allocations).  Same request semantics, formats and output layout as
+ * mtgp_generate_u32/_f32 (`out` is a device pointer of sum(counts) 4-byte
+ * elements); at most 1024 requests per call, more is MTGP_EINVAL.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine: the work table lives
+ * in a 64 KiB statically declared device array that every device loading the
+ * library holds until exit.  The first call on a device looks that array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the array and each overwrites the
+ * previous contents (the claim counters are cleared on every call), so calls
+ * whose kernels overlap on the GPU race: order them (one CUDA stream, one
+ * host thread at a time).  Asynchronous on cuda_stream. */
+mtgp_status mtgp_generate_noalloc(mtgp_streams_t streams, const uint32_t* stream_ids,
+                                  const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
+                                  void* out, void* cuda_stream);
+
 /* Waits for cuda_stream and reads the device error word of this handle.
  * MTGP_EDEVICE if a kernel recorded an inconsistency since the last check
  * (the word is then cleared). */

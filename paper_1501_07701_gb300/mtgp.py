@@ -89,6 +89,7 @@ _SIGS = {
     "mtgp_generate_f32": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP, _VP],
     "mtgp_generate_to_host": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP,
                               ctypes.c_uint64, _VP],
+    "mtgp_generate_noalloc": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP, _VP],
     "mtgp_check": [_VP, _VP],
     "mtgp_streams_free": [_VP],
     "mtgp_get_launch_config": [_VP, ctypes.POINTER(LaunchConfig)],
@@ -338,6 +339,16 @@ def mtgp_generate_to_host(streams: Streams, stream_ids, counts, fmt, host_out, c
         ptr = host_out.data_ptr()
     _call("mtgp_generate_to_host", streams.handle, _p32(ids), _p64(counts), ids.size, int(fmt),
           ptr, int(chunk_bytes), _stream_handle(stream))
+
+
+def mtgp_generate_noalloc(streams: Streams, stream_ids, counts, fmt, out, stream=None):
+    """mtgp_generate_u32/_f32 without any allocation (work table in a static
+    device array; at most 1024 requests; calls on one device must not
+    overlap on the GPU)."""
+    ids, counts = _req_arrays(stream_ids, counts)
+    total = int(counts.sum()) if counts.size else 0
+    _call("mtgp_generate_noalloc", streams.handle, _p32(ids), _p64(counts), ids.size, int(fmt),
+          _dev_ptr(out, total), _stream_handle(stream))
 
 
 def mtgp_check(streams: Streams, stream=None):
