@@ -69,6 +69,9 @@ def workload(name: str, rank: int, streams: int = 0, count: int = 0):
         w = workloads.uneven()
         desc = ("uneven: 10000 MTGP32 Mexp 11213 streams, counts floor(2^U), U~U[10,22] "
                 "(seed 7)")
+        if streams:
+            w = {"mexp": w["mexp"], "seeds": w["seeds"][:streams], "counts": w["counts"][:streams]}
+            desc = "uneven subset: first %d of the 10000 streams" % streams
     elif name == "equal":
         w = workloads.equal(streams or 4096, count or (1 << 18))
         desc = "equal: %d MTGP32 Mexp 11213 streams x %d" % (streams or 4096, count or (1 << 18))
@@ -206,9 +209,13 @@ def run_ours(args, rank, world, local_rank):
     st = mtgp.mtgp_init_statuses(params, w["seeds"], stream)
     out = torch.empty(total, dtype=torch.int32, device=dev)
     ids = np.arange(w["seeds"].size, dtype=np.uint32)
+    if args.config:
+        cv = [int(v) for v in args.config.split(",")] + [0]
+        mtgp.mtgp_set_launch_config(st, warps_per_cta=cv[0], words_per_lane=cv[1],
+                                    coop_percent=cv[2], ctas_per_sm=cv[3])
     plan = mtgp.mtgp_plan_create(st, ids, counts, mtgp.MTGP_U32, out)
     tuned = None
-    if not args.no_autotune:
+    if not args.no_autotune and not args.config:
         tuned = mtgp.mtgp_plan_autotune(plan)
     info = mtgp.mtgp_plan_get_info(plan)
 
@@ -310,6 +317,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "20 GB written per step (> 129 MB L2) plus a 256 MiB rewrite "
                              "between timed steps",
                        "launch": info["config"], "grid_ctas": info["grid_ctas"],
+                       "coop_streams": info["n_coop"], "regs_per_thread": info["regs_per_thread"],
+                       "resident_ctas_per_sm": info["resident_ctas_per_sm"],
                        "autotuned": tuned is not None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(),
@@ -398,6 +407,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the serving trace (0 = skip the serving measurement)")
+    ap.add_argument("--config", default="",
+                    help="force warps_per_cta,words_per_lane,coop_percent[,ctas_per_sm] (skips autotuning)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -241,6 +241,8 @@ typedef struct {
     mtgp_launch_config config;
     uint32_t grid_ctas;
     uint32_t n_coop;          /* streams advanced by whole CTAs                 */
+    uint32_t regs_per_thread; /* of the generation kernel                       */
+    uint32_t resident_ctas_per_sm;
 } mtgp_plan_info;
 
 /* Times the tuning candidates on this plan's own work table, on a scratch
@@ -248,6 +250,18 @@ typedef struct {
  * buffer is overwritten), installs the fastest in the plan and re-records its
  * graph.  Synchronous. */
 mtgp_status mtgp_plan_autotune(mtgp_plan_t plan, mtgp_launch_config* best);
+
+/* Timeline of the plan's launches (diagnostics; no counterpart in the
+ * paper).  enable = 1 allocates a device record of 4 words per stream of the
+ * plan and re-records the graph so that every later launch stores, for each
+ * stream in the plan's table order (longest first): the start and end time
+ * of its generation (%globaltimer, ns), the SM it ran on, and its count.
+ * enable = 0 drops the record.  Synchronous. */
+mtgp_status mtgp_plan_set_trace(mtgp_plan_t plan, int enable);
+
+/* Copies the record of the last launch to the host array `host` of
+ * 4 * n_items uint64 (n_items from mtgp_plan_get_info). */
+mtgp_status mtgp_plan_read_trace(mtgp_plan_t plan, uint64_t* host);
 
 mtgp_status mtgp_plan_get_info(mtgp_plan_t plan, mtgp_plan_info* info);
 mtgp_status mtgp_plan_free(mtgp_plan_t plan);

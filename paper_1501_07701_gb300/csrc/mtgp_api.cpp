@@ -117,6 +117,7 @@ static void to_kparams(const mtgp_params_desc& d, KParams& k)
     k.sh1 = d.sh1;
     k.sh2 = d.sh2;
     k.mask = d.mask;
+    k.mirror = 32u * ((d.pos + 31u + 31u) / 32u);
     for (int i = 0; i < 16; ++i) {
         k.rec[i] = d.rec_tbl[i];
         k.tmp[i] = d.tmp_tbl[i];
@@ -592,8 +593,9 @@ mtgp_status mtgp::geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t 
         st->geo_valid = true;
     }
     *g = st->geo_cap;
-    const long long warps = g->threads / 32;
-    const long long want = ((long long)n_items + warps - 1) / warps;
+    // One CTA per item at most (a CTA may take a whole stream); CTAs that find
+    // no work left exit at once.
+    const long long want = (long long)n_items;
     g->grid = (int)std::max(1LL, std::min<long long>(want, st->geo_cap.grid));
     return MTGP_OK;
 }
@@ -653,6 +655,7 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
     a.counter = (uint32_t*)sl.dev;
     a.out = (uint32_t*)out;
     a.err = st->d_err;
+    a.trace = nullptr;
     CUDA_TRY(launch_generate(a, g, s), "generation kernel launch");
     CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
     sl.ev_recorded = true;
@@ -1057,6 +1060,7 @@ static mtgp_status record_graph(mtgp_plan* p)
     a.counter = (uint32_t*)p->d_table;
     a.out = (uint32_t*)p->out;
     a.err = p->st->d_err;
+    a.trace = p->d_trace;
     cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, p->geo, cap) : e1;
     cudaGraph_t graph = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(cap, &graph);
@@ -1086,6 +1090,8 @@ static void destroy_plan(mtgp_plan* p)
         cudaStreamDestroy(p->cap_stream);
     if (p->d_table)
         cudaFree(p->d_table);
+    if (p->d_trace)
+        cudaFree(p->d_trace);
     delete p;
 }
 
@@ -1203,6 +1209,43 @@ extern "C" mtgp_status mtgp_plan_autotune(mtgp_plan_t p, mtgp_launch_config* bes
     GUARD_END
 }
 
+extern "C" mtgp_status mtgp_plan_set_trace(mtgp_plan_t p, int enable)
+{
+    GUARD_BEGIN
+    if (!p)
+        return fail(MTGP_EINVAL, "null plan");
+    DeviceGuard g(p->st->device);
+    CUDA_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (enable && !p->d_trace && p->n_items) {
+        CUDA_TRY(cudaMalloc(&p->d_trace, (size_t)p->n_items * 4 * sizeof(uint64_t)),
+                 "cudaMalloc(trace)");
+        CUDA_TRY(cudaMemset(p->d_trace, 0, (size_t)p->n_items * 4 * sizeof(uint64_t)), "cudaMemset");
+    } else if (!enable && p->d_trace) {
+        cudaFree(p->d_trace);
+        p->d_trace = nullptr;
+    }
+    mtgp_status r = record_graph(p);
+    if (r != MTGP_OK)
+        return r;
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_plan_read_trace(mtgp_plan_t p, uint64_t* host)
+{
+    GUARD_BEGIN
+    if (!p || !host)
+        return fail(MTGP_EINVAL, "null argument");
+    if (!p->d_trace)
+        return fail(MTGP_EINVAL, "tracing is not enabled on this plan");
+    DeviceGuard g(p->st->device);
+    CUDA_TRY(cudaMemcpy(host, p->d_trace, (size_t)p->n_items * 4 * sizeof(uint64_t),
+                        cudaMemcpyDeviceToHost),
+             "cudaMemcpy(trace)");
+    return ok();
+    GUARD_END
+}
+
 extern "C" mtgp_status mtgp_plan_get_info(mtgp_plan_t p, mtgp_plan_info* info)
 {
     if (!p || !info)
@@ -1216,6 +1259,8 @@ extern "C" mtgp_status mtgp_plan_get_info(mtgp_plan_t p, mtgp_plan_info* info)
     info->config = to_public(eff);
     info->grid_ctas = (uint32_t)p->geo.grid;
     info->n_coop = p->n_coop;
+    info->regs_per_thread = (uint32_t)p->geo.regs;
+    info->resident_ctas_per_sm = (uint32_t)p->geo.per_sm;
     return ok();
 }
 

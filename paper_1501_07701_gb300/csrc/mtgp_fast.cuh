@@ -15,16 +15,14 @@
 //   * Column group m (columns 32m .. 32m+31) belongs to one warp; lane l of
 //     that warp keeps column 32m + l in a register (word i).
 //   * The latest value of every column is also published in a shared-memory
-//     row S[0..N), with a mirror S[N..N+32) of columns 0..31 and a guard
-//     S[-1] of column N-1.  Words i+1, i+pos and i+pos-1 of 32 consecutive
-//     columns are then plain conflict-free loads at S[c+1], S[c+pos],
-//     S[c+pos-1] with no modulo (the mirror supplies the wrapped columns).
-//   * The recursion and tempering tables live in lane registers (lane l holds
-//     entry l & 15); a lookup is one shuffle whose source lane is the index
-//     itself (shfl uses the low five bits of the lane operand).
-//   * Shifts are done as integer multiplies (x << s = x * 2^s and x >> s =
-//     high word of x * 2^(32-s)), which run on the FMA pipe and leave the ALU
-//     pipe to the XORs.
+//     row S[0..N), followed by a mirror S[N..N+E) of columns 0..E-1,
+//     E >= pos + 31.  Words i+1, i+pos and i+pos-1 of 32 consecutive columns
+//     are then plain conflict-free loads at S[c+1], S[c+pos], S[c+pos-1]
+//     with no modulo and no bounds arithmetic: a pick-up past column N-1
+//     lands in the mirror, which holds the new row's value of that column.
+//   * The recursion and tempering tables are 16-word shared arrays whose entry
+//     k sits in bank k, so a warp's 32 lookups are one conflict-free
+//     shared-memory wavefront whatever the indices.
 //
 // A sub-step m computes columns 32m..32m+31 of the next row (one new word per
 // lane).  K consecutive sub-steps form one parallel step of 32K words; when
@@ -45,41 +43,52 @@ __device__ __forceinline__ void cp_async16(uint32_t* smem_dst, const uint32_t* g
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t sm_id()
+{
+    uint32_t v;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+    return v;
+}
+
+// Timeline record of one item (only when a trace buffer is given).
+__device__ __forceinline__ void trace_item(uint64_t* trace, uint32_t it, uint64_t t0,
+                                           const Segment* segs, const WorkItem& w)
+{
+    const Segment last = segs[w.seg_begin + w.nseg - 1u];
+    trace[4u * it + 0] = t0;
+    trace[4u * it + 1] = global_ns();
+    trace[4u * it + 2] = sm_id();
+    trace[4u * it + 3] = last.g_start + last.count;
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Multipliers for the shifts (sh1, sh2 in 1..31): y << sh1 = y * m1,
-// x >> sh2 = umulhi(x, m2).
-struct Shifts {
-    uint32_t m1, m2;
-};
-
-__device__ __forceinline__ Shifts make_shifts(const KParams& P)
+// Tables in shared memory: 16 words each, at a 64-byte aligned base, so
+// that entry k of a table sits in bank k and any lookup pattern of a warp is
+// one conflict-free wavefront.  Tb[0..16) recursion, Tb[16..32) tempering,
+// Tb[32..48) float tempering.
+__device__ __forceinline__ uint32_t tbl(const uint32_t* Tb, uint32_t base, uint32_t idx)
 {
-    Shifts s;
-    s.m1 = 1u << P.sh1;
-    s.m2 = 1u << (32u - P.sh2);
-    return s;
+    return Tb[base + (idx & 15u)];
 }
 
-// The new word of one column from words i (own register), i+1, i+pos.
-__device__ __forceinline__ uint32_t recur(uint32_t xi, uint32_t x1, uint32_t xp, uint32_t mask,
-                                          const Shifts& sh, uint32_t tR)
-{
-    uint32_t y = (xi & mask) ^ x1;
-    y = y ^ (y * sh.m1) ^ __umulhi(xp, sh.m2);
-    return y ^ __shfl_sync(MTGP_FULL, tR, y);
-}
-
-// Tempering index from word i+pos-1: fold >> 16 then >> 8 (low four bits
-// are used; the shuffle ignores bit 4 because the tables repeat).
+// Tempering index from word i+pos-1: fold >> 16 then >> 8; the low four bits
+// select the entry.
 __device__ __forceinline__ uint32_t temper_index(uint32_t xq)
 {
-    const uint32_t t = xq ^ __umulhi(xq, 1u << 16);
-    return t ^ __umulhi(t, 1u << 24);
+    const uint32_t t = xq ^ (xq >> 16);
+    return t ^ (t >> 8);
 }
 
 // Output conversion from the new word v and the tempering index ti.
@@ -87,19 +96,18 @@ __device__ __forceinline__ uint32_t temper_index(uint32_t xq)
 //   FMT 1: (v >> 9) ^ FLT[ti]   == 0x3F800000 | ((v ^ TMP[ti]) >> 9)
 //   FMT 2: the FMT 1 float minus 1.0f (exact: Sterbenz)
 template <int FMT>
-__device__ __forceinline__ uint32_t temper_convert(uint32_t v, uint32_t ti, uint32_t tT, uint32_t tF)
+__device__ __forceinline__ uint32_t temper_convert(uint32_t v, uint32_t ti, const uint32_t* Tb)
 {
     if (FMT == 0)
-        return v ^ __shfl_sync(MTGP_FULL, tT, ti);
-    const uint32_t b = __umulhi(v, 1u << 23) ^ __shfl_sync(MTGP_FULL, tF, ti);
+        return v ^ tbl(Tb, 16u, ti);
+    const uint32_t b = (v >> 9) ^ tbl(Tb, 32u, ti);
     if (FMT == 1)
         return b;
     return __float_as_uint(__uint_as_float(b) - 1.0f);
 }
 
-// Per-lane output of the slow path: the lane finds its request and format.
-// ou / of are the u32 and [1,2) outputs, both computed while the warp was
-// converged (they need shuffles); this function itself is lane-local.
+// Per-lane output of the slow path: the lane finds its request and format
+// (ou / of are the u32 and [1,2) outputs).
 __device__ __forceinline__ void slow_store(uint32_t ou, uint32_t of, uint64_t g,
                                            const Segment* __restrict__ segs, uint32_t s_first,
                                            uint32_t s_end, uint32_t* __restrict__ out)
@@ -125,15 +133,14 @@ __device__ __forceinline__ void slow_store(uint32_t ou, uint32_t of, uint64_t g,
 // advancing the stream (WG = 1 for a warp-owned stream); that warp keeps
 // columns 32m + lane in register r[m / WG].  `Sw` = S + 32*warp + lane.
 //
-// Every shuffle (table lookups) runs in the read phase, under conditions that
-// are uniform across the warp; the write phase is lane-predicated and holds
-// no warp-synchronous instruction.
+// No warp-synchronous instruction is executed under a lane-dependent
+// condition: the write phase is lane-predicated and holds only stores.
 // ===========================================================================
 template <int M, int K, int WG, int FMT, bool SLOW>
 __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32_t* __restrict__ S,
                                         uint32_t* __restrict__ Sw, uint32_t* __restrict__ ow,
-                                        const KParams& P, const Shifts& sh, uint32_t warp,
-                                        uint32_t lane, uint32_t tR, uint32_t tT, uint32_t tF,
+                                        const uint32_t* __restrict__ Q, const KParams& P,
+                                        uint32_t warp, uint32_t lane, const uint32_t* __restrict__ Tb,
                                         uint32_t last_lane, uint32_t n_valid, uint64_t row_g,
                                         const Segment* __restrict__ segs, uint32_t s_first,
                                         uint32_t s_end, uint32_t* __restrict__ out)
@@ -144,26 +151,47 @@ __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32
     for (int s0 = 0; s0 < M; s0 += K) {
         if (SLOW && 32u * (uint32_t)s0 >= n_valid)
             break;
-        uint32_t xn[PER], o1[PER], o2[PER];
+        // The read phase runs in stages across the PER sub-steps (all loads,
+        // then all recursion arithmetic, then all table lookups, ...) so that
+        // the sub-steps' latencies overlap.
+        bool on[PER];
+        uint32_t x1[PER], xp[PER], xq[PER], y[PER], xn[PER], ti[PER], o1[PER], o2[PER];
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int j = s0 / WG + i;
             const uint32_t m = (uint32_t)(s0 + i * WG) + (WG > 1 ? warp : 0u);
-            if (j < J && m < (uint32_t)M) {   // uniform across the warp
-                const int off = 32 * (s0 + i * WG);            // static part of 32m
-                uint32_t sp = P.pos + 32u * m;                  // (pos + 32m) mod N
-                sp = sp >= P.n ? sp - P.n : sp;
-                const uint32_t* q = S + sp + lane;
-                xn[i] = recur(r[j], Sw[off + 1], q[0], P.mask, sh, tR);
-                const uint32_t ti = temper_index(q[-1]);
-                if (SLOW) {
-                    o1[i] = temper_convert<0>(xn[i], ti, tT, tF);
-                    o2[i] = temper_convert<1>(xn[i], ti, tT, tF);
-                } else {
-                    o1[i] = temper_convert<FMT>(xn[i], ti, tT, tF);
-                }
+            on[i] = j < J && m < (uint32_t)M;   // uniform across the warp
+            if (on[i]) {
+                const int off = 32 * (s0 + i * WG);   // static part of 32m
+                x1[i] = Sw[off + 1];    // word i+1
+                xp[i] = Q[off];         // word i+pos   (Q = S + pos + 32*warp + lane)
+                xq[i] = Q[off - 1];     // word i+pos-1
             }
         }
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (on[i]) {
+                const uint32_t yy = (r[s0 / WG + i] & P.mask) ^ x1[i];
+                y[i] = yy ^ (yy << P.sh1) ^ (xp[i] >> P.sh2);
+            }
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (on[i])
+                xn[i] = y[i] ^ tbl(Tb, 0u, y[i]);
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (on[i])
+                ti[i] = temper_index(xq[i]);
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (on[i]) {
+                if (SLOW) {
+                    o1[i] = temper_convert<0>(xn[i], ti[i], Tb);
+                    o2[i] = temper_convert<1>(xn[i], ti[i], Tb);
+                } else {
+                    o1[i] = temper_convert<FMT>(xn[i], ti[i], Tb);
+                }
+            }
         if (WG > 1)
             __syncthreads();
         else
@@ -179,10 +207,8 @@ __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32
                 if (act) {
                     r[j] = xn[i];
                     Sw[off] = xn[i];
-                    if (m == 0)
-                        S[P.n + lane] = xn[i];
-                    if (col == P.n - 1u)
-                        S[-1] = xn[i];
+                    if (32u * m < P.mirror)
+                        Sw[off + P.n] = xn[i];
                     if (SLOW)
                         slow_store(o1[i], o2[i], row_g + col, segs, s_first, s_end, out);
                     else
@@ -203,13 +229,12 @@ template <int M, int K, int WG>
 __device__ __forceinline__ void run_item(const KParams& P, uint32_t* __restrict__ g, uint32_t* __restrict__ S,
                                          const Segment* __restrict__ segs, uint32_t s_begin,
                                          uint32_t s_end, uint32_t* __restrict__ out, uint32_t warp,
-                                         uint32_t lane, uint32_t tR, uint32_t tT, uint32_t tF)
+                                         uint32_t lane, const uint32_t* __restrict__ Tb)
 {
     constexpr int J = (M + WG - 1) / WG;
     const uint32_t N = P.n;
     const uint32_t tid = WG > 1 ? threadIdx.x : lane;
     const uint32_t wk = WG > 1 ? warp : 0u;
-    const Shifts sh = make_shifts(P);
     const uint32_t last_lane = (N - 1u) & 31u;   // lane of column N-1 (group M-1)
 
     // stage in: the state row (HBM) -> S through 16-byte cp.async
@@ -226,16 +251,10 @@ __device__ __forceinline__ void run_item(const KParams& P, uint32_t* __restrict_
         const uint32_t c = 32u * (wk + (uint32_t)(j * WG)) + lane;
         r[j] = c < N ? S[c] : 0u;
     }
-    const uint32_t mirror = S[lane];
-    const uint32_t guard = S[N - 1u];
-    if (WG > 1)
-        __syncthreads();
-    else
-        __syncwarp();
-    if (wk == 0) {
-        S[N + lane] = mirror;
-        if (lane == 0)
-            S[-1] = guard;
+    // mirror: columns 0 .. P.mirror-1 again at S[N ..]
+    for (uint32_t c = tid; c < P.mirror; c += 32u * WG) {
+        const uint32_t v = S[c];
+        S[N + c] = v;
     }
     if (WG > 1)
         __syncthreads();
@@ -243,28 +262,35 @@ __device__ __forceinline__ void run_item(const KParams& P, uint32_t* __restrict_
         __syncwarp();
 
     uint32_t* Sw = S + 32u * wk + lane;
+    const uint32_t* Q = S + P.pos + 32u * wk + lane;
     const Segment last = segs[s_end - 1u];
     const uint64_t total = last.g_start + last.count;
+    // The current request stays in registers: rows only touch the table
+    // when they cross into the next request (a dependent global load per row
+    // would put an L2 round trip on every row's critical path).
     uint32_t s = s_begin;
+    Segment sg = segs[s];
+    uint64_t seg_end = sg.g_start + sg.count;
     for (uint64_t row = 0; row < total; row += N) {
-        while (segs[s].g_start + segs[s].count <= row)
-            ++s;
-        const Segment sg = segs[s];
+        while (row >= seg_end) {
+            sg = segs[++s];
+            seg_end = sg.g_start + sg.count;
+        }
         const uint64_t left = total - row;
         const uint32_t n_valid = left < (uint64_t)N ? (uint32_t)left : N;
-        if (n_valid == N && row + N <= sg.g_start + sg.count) {
+        if (n_valid == N && row + N <= seg_end) {
             uint32_t* ow = out + sg.out_off + (row - sg.g_start) + 32u * wk + lane;
             if (sg.fmt == 0)
-                gen_row<M, K, WG, 0, false>(r, S, Sw, ow, P, sh, wk, lane, tR, tT, tF, last_lane, N, row,
+                gen_row<M, K, WG, 0, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
                                             segs, s, s_end, out);
             else if (sg.fmt == 1)
-                gen_row<M, K, WG, 1, false>(r, S, Sw, ow, P, sh, wk, lane, tR, tT, tF, last_lane, N, row,
+                gen_row<M, K, WG, 1, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
                                             segs, s, s_end, out);
             else
-                gen_row<M, K, WG, 2, false>(r, S, Sw, ow, P, sh, wk, lane, tR, tT, tF, last_lane, N, row,
+                gen_row<M, K, WG, 2, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
                                             segs, s, s_end, out);
         } else {
-            gen_row<M, K, WG, 0, true>(r, S, Sw, nullptr, P, sh, wk, lane, tR, tT, tF, last_lane, n_valid,
+            gen_row<M, K, WG, 0, true>(r, S, Sw, nullptr, Q, P, wk, lane, Tb, last_lane, n_valid,
                                        row, segs, s, s_end, out);
         }
     }
@@ -294,15 +320,20 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
                                                            const Segment* __restrict__ segs,
                                                            uint32_t n_items, uint32_t n_coop,
                                                            uint32_t* __restrict__ counters,
-                                                           uint32_t* __restrict__ out, int* __restrict__ err)
+                                                           uint32_t* __restrict__ out, int* __restrict__ err,
+                                                           uint64_t* __restrict__ trace)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_claim;
+    __shared__ __align__(64) uint32_t Tb[48];
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t tR = P.rec[lane & 15u];
-    const uint32_t tT = P.tmp[lane & 15u];
-    const uint32_t tF = P.flt[lane & 15u];
+    if (threadIdx.x < 16) {
+        Tb[threadIdx.x] = P.rec[threadIdx.x];
+        Tb[16 + threadIdx.x] = P.tmp[threadIdx.x];
+        Tb[32 + threadIdx.x] = P.flt[threadIdx.x];
+    }
+    __syncthreads();
 
     for (;;) {
         if (threadIdx.x == 0)
@@ -318,11 +349,14 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
                 atomicOr(err, 1);
             continue;
         }
-        run_item<M, K, G>(P, states + (size_t)w.stream * P.np, smem + 4, segs, w.seg_begin,
-                          w.seg_begin + w.nseg, out, warp, lane, tR, tT, tF);
+        const uint64_t t0 = trace ? global_ns() : 0;
+        run_item<M, K, G>(P, states + (size_t)w.stream * P.np, smem, segs, w.seg_begin,
+                          w.seg_begin + w.nseg, out, warp, lane, Tb);
+        if (trace && threadIdx.x == 0)
+            trace_item(trace, it, t0, segs, w);
     }
 
-    uint32_t* S = smem + warp * fast_smem_words(P.n) + 4;
+    uint32_t* S = smem + warp * fast_smem_words(P.n, P.mirror);
     for (;;) {
         uint32_t it = 0;
         if (lane == 0)
@@ -336,8 +370,11 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
                 atomicOr(err, 1);
             continue;
         }
+        const uint64_t t0 = trace ? global_ns() : 0;
         run_item<M, K, 1>(P, states + (size_t)w.stream * P.np, S, segs, w.seg_begin,
-                          w.seg_begin + w.nseg, out, warp, lane, tR, tT, tF);
+                          w.seg_begin + w.nseg, out, warp, lane, Tb);
+        if (trace && lane == 0)
+            trace_item(trace, it, t0, segs, w);
     }
 }
 

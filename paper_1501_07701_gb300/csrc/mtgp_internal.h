@@ -15,6 +15,8 @@ struct KParams {
     uint32_t n;      // state words N
     uint32_t np;     // HBM row stride in words: N rounded up to 4 (16-byte rows)
     uint32_t pos, sh1, sh2, mask;
+    uint32_t mirror; // columns repeated after S[N) by the register-resident kernel:
+                     // 32 * ceil((pos + 31) / 32)
     uint32_t rec[16];
     uint32_t tmp[16];
     uint32_t flt[16];
@@ -51,10 +53,13 @@ struct LaunchCfg {
 };
 
 // Per-warp shared-memory footprint (32-bit words).
-//   fast: 3 pad words + guard S[-1], then S[0 .. N+32) rounded up to 4 words,
-//         so that S is 16-byte aligned for the cp.async stage-in.
+//   fast: S[0 .. N + mirror) rounded up to 4 words (16-byte aligned rows for
+//         the cp.async stage-in).
 //   ring: S[0 .. N) rounded up to 4 words.
-__host__ __device__ inline uint32_t fast_smem_words(uint32_t n) { return 4u + ((n + 32u + 3u) & ~3u); }
+__host__ __device__ inline uint32_t fast_smem_words(uint32_t n, uint32_t mirror)
+{
+    return (n + mirror + 3u) & ~3u;
+}
 __host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return (n + 3u) & ~3u; }
 
 // True if the register-resident kernel has an instantiation for this N, k
@@ -77,6 +82,7 @@ struct GenArgs {
     uint32_t* counter;   // two claim counters, zeroed before the launch
     uint32_t* out;
     int* err;
+    uint64_t* trace;     // optional: 4 words per item (start ns, end ns, SM, numbers)
 };
 
 // Resolved launch geometry for a configuration.
@@ -86,6 +92,8 @@ struct Geometry {
     int threads;
     size_t smem;
     int grid;
+    int regs;            // registers per thread of the kernel used
+    int per_sm;          // resident CTAs per SM (occupancy, after the cap)
 };
 
 // Works out kernel choice, block size, shared memory and grid (persistent:

@@ -201,7 +201,7 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
     g->threads = warps * 32;
     const void* fn;
     if (kernel == 0) {
-        g->smem = (size_t)warps * fast_smem_words(P.n) * 4u;
+        g->smem = (size_t)warps * fast_smem_words(P.n, P.mirror) * 4u;
         fn = fast_kernel_ptr(fast_m(P), k, warps);
     } else {
         g->smem = (size_t)(32u + warps * ring_smem_words(P.n)) * 4u;
@@ -221,6 +221,12 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
         return cudaErrorInvalidConfiguration;
     if (cfg.ctas_per_sm > 0)
         per_sm = std::min(per_sm, cfg.ctas_per_sm);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess)
+        return e;
+    g->regs = fa.numRegs;
+    g->per_sm = per_sm;
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess)
@@ -277,7 +283,9 @@ cudaError_t launch_fast(int M, int K, int G, const GenArgs& a, dim3 grid, dim3 b
     uint32_t* counter = a.counter;
     uint32_t* out = a.out;
     int* err = a.err;
-    void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &n_coop, &counter, &out, &err};
+    uint64_t* trace = a.trace;
+    void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &n_coop, &counter, &out, &err,
+                    &trace};
     return cudaLaunchKernel(fn, grid, block, args, smem, s);
 }
 

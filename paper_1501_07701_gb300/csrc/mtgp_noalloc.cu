@@ -192,6 +192,7 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
     a.counter = reinterpret_cast<uint32_t*>(scratch);
     a.out = (uint32_t*)out;
     a.err = st->d_err;
+    a.trace = nullptr;
     e = launch_generate(a, g, cs);
     if (e != cudaSuccess)
         return fail_cuda(e, "generation kernel launch (no-alloc)");

@@ -86,6 +86,7 @@ struct mtgp_plan {
     mtgp::Geometry geo{};
     mtgp::Work work;
     void* d_table = nullptr;
+    uint64_t* d_trace = nullptr;   // optional per-item timeline
     size_t items_off = 0, segs_off = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;

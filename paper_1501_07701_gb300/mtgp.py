@@ -50,7 +50,8 @@ class LaunchConfig(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("total_numbers", ctypes.c_uint64), ("n_items", ctypes.c_uint32),
                 ("kernel_launches", ctypes.c_uint32), ("config", LaunchConfig),
-                ("grid_ctas", ctypes.c_uint32), ("n_coop", ctypes.c_uint32)]
+                ("grid_ctas", ctypes.c_uint32), ("n_coop", ctypes.c_uint32),
+                ("regs_per_thread", ctypes.c_uint32), ("resident_ctas_per_sm", ctypes.c_uint32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -101,6 +102,8 @@ _SIGS = {
     "mtgp_plan_launch": [_VP, _VP],
     "mtgp_plan_autotune": [_VP, ctypes.POINTER(LaunchConfig)],
     "mtgp_plan_get_info": [_VP, ctypes.POINTER(PlanInfo)],
+    "mtgp_plan_set_trace": [_VP, ctypes.c_int],
+    "mtgp_plan_read_trace": [_VP, _U64P],
     "mtgp_plan_free": [_VP],
     "mtgp_server_create": [_VP, ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)],
     "mtgp_server_submit": [_VP, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64],
@@ -392,12 +395,25 @@ def mtgp_plan_autotune(plan: Plan) -> dict:
     return c.as_dict()
 
 
+def mtgp_plan_set_trace(plan: Plan, enable: bool = True):
+    _call("mtgp_plan_set_trace", plan.handle, int(bool(enable)))
+
+
+def mtgp_plan_read_trace(plan: Plan) -> np.ndarray:
+    """(n_items, 4) uint64: start ns, end ns, SM, numbers -- table order."""
+    n = mtgp_plan_get_info(plan)["n_items"]
+    out = np.zeros((max(n, 1), 4), np.uint64)
+    _call("mtgp_plan_read_trace", plan.handle, _p64(out))
+    return out[:n]
+
+
 def mtgp_plan_get_info(plan: Plan) -> dict:
     i = PlanInfo()
     _call("mtgp_plan_get_info", plan.handle, ctypes.byref(i))
     return {"total_numbers": i.total_numbers, "n_items": i.n_items,
             "kernel_launches": i.kernel_launches, "config": i.config.as_dict(),
-            "grid_ctas": i.grid_ctas, "n_coop": i.n_coop}
+            "grid_ctas": i.grid_ctas, "n_coop": i.n_coop, "regs_per_thread": i.regs_per_thread,
+            "resident_ctas_per_sm": i.resident_ctas_per_sm}
 
 
 class Server:
