@@ -518,7 +518,7 @@ LaunchCfg mtgp::default_config(const KParams& P)
     c.ctas_per_sm = 0;
     c.k = 8;
     c.kernel = 0;
-    c.coop_percent = 100;
+    c.coop_percent = 0;
     if (!fast_supported(P, 8))
         c.k = fast_supported(P, 4) ? 4 : 8;
     return c;
@@ -879,21 +879,33 @@ extern "C" mtgp_status mtgp_set_launch_config(mtgp_streams_t st, const mtgp_laun
 
 std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
 {
+    // Residency matters as much as block shape: a launch whose longest
+    // streams dominate runs best with few warps per SM (each stream gets a
+    // larger share of the SM), an even launch with many.  Candidates cover
+    // 4 .. 24 warps per SM, with and without the whole-CTA mode for long
+    // streams.
     std::vector<LaunchCfg> v;
-    for (int k : {8, 4})
-        for (int w : {2, 4, 8}) {
-            if (!fast_supported(P, k, w))
-                continue;
-            for (int coop : {0, 50, 100, 200}) {
-                LaunchCfg x;
-                x.warps_per_cta = w;
-                x.ctas_per_sm = 0;
-                x.k = k;
-                x.kernel = 0;
-                x.coop_percent = coop;
-                v.push_back(x);
-            }
-        }
+    auto add = [&](int w, int k, int cap, int coop) {
+        if (!fast_supported(P, k, w))
+            return;
+        LaunchCfg x;
+        x.warps_per_cta = w;
+        x.ctas_per_sm = cap;
+        x.k = k;
+        x.kernel = 0;
+        x.coop_percent = coop;
+        v.push_back(x);
+    };
+    for (int k : {8, 4}) {
+        for (int cap : {1, 2, 3, 4, 0})
+            add(4, k, cap, 0);
+        for (int cap : {2, 3, 4, 6, 0})
+            add(2, k, cap, 0);
+        add(8, k, 1, 0);
+        add(8, k, 0, 0);
+        add(4, k, 0, 100);
+        add(8, k, 1, 100);
+    }
     if (v.empty()) {   // no register-resident instantiation: tune the ring kernel
         for (int w : {2, 4, 8}) {
             LaunchCfg x;
