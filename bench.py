@@ -39,7 +39,8 @@ METRIC = "Gnumbers/s and % of HBM-write roofline, bit-exact; serving p50/p99 lat
 UNIT = "Gnumbers/s"
 KERNEL_SOURCES = ["paper_1501_07701_gb300/csrc/mtgp_fast.cuh",
                   "paper_1501_07701_gb300/csrc/mtgp_kernels.cu"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fast_kernel_uneven_traffic.md")
+KERNEL_NAMES = {0: "mtgp_fast_kernel", 1: "mtgp_ring_kernel"}
+FORMATS = {"u32": 0, "f12": 1, "f01": 2}
 
 
 def kernel_source_hash() -> str:
@@ -50,11 +51,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+def recorded_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per launch of the uneven workload from the committed ncu
+    summary of that kernel, if it was taken on the current kernel source;
+    else None."""
+    if workload_name != "uneven":
+        return None
+    path = os.path.join(ROOT, "profiles", kernel.replace("mtgp_", "") + "_uneven_traffic.md")
     try:
-        txt = open(TRAFFIC_FILE).read()
+        txt = open(path).read()
     except OSError:
         return None
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
@@ -72,6 +77,9 @@ def workload(name: str, rank: int, streams: int = 0, count: int = 0):
         if streams:
             w = {"mexp": w["mexp"], "seeds": w["seeds"][:streams], "counts": w["counts"][:streams]}
             desc = "uneven subset: first %d of the 10000 streams" % streams
+    elif name == "single":
+        w = workloads.single()
+        desc = "single: 1 MTGP32 Mexp 11213 stream (seed 1) x 2^20"
     elif name == "equal":
         w = workloads.equal(streams or 4096, count or (1 << 18))
         desc = "equal: %d MTGP32 Mexp 11213 streams x %d" % (streams or 4096, count or (1 << 18))
@@ -210,10 +218,11 @@ def run_ours(args, rank, world, local_rank):
     out = torch.empty(total, dtype=torch.int32, device=dev)
     ids = np.arange(w["seeds"].size, dtype=np.uint32)
     if args.config:
-        cv = [int(v) for v in args.config.split(",")] + [0]
+        cv = [int(v) for v in args.config.split(",")] + [0, 0]
         mtgp.mtgp_set_launch_config(st, warps_per_cta=cv[0], words_per_lane=cv[1],
-                                    coop_percent=cv[2], ctas_per_sm=cv[3])
-    plan = mtgp.mtgp_plan_create(st, ids, counts, mtgp.MTGP_U32, out)
+                                    coop_percent=cv[2], ctas_per_sm=cv[3], kernel=cv[4])
+    fmt = FORMATS[args.format]
+    plan = mtgp.mtgp_plan_create(st, ids, counts, fmt, out)
     tuned = None
     if not args.no_autotune and not args.config:
         tuned = mtgp.mtgp_plan_autotune(plan)
@@ -228,7 +237,7 @@ def run_ours(args, rank, world, local_rank):
             mtgp.mtgp_plan_launch(plan, stream)
             if _ == 0 and rank == 0:
                 stream.synchronize()
-                bit_exact = spot_check(w, counts, out, states0)
+                bit_exact = spot_check(w, counts, out, states0, fmt)
             flush.fill_(1)
     stream.synchronize()
 
@@ -276,6 +285,7 @@ def run_ours(args, rank, world, local_rank):
     n_words = mtgp.mtgp_streams_info(st)[1]
     alg_bytes = 4.0 * total + 8.0 * n_words * info["n_items"]
     kern_avg = sum(kern_ms) / len(kern_ms) / 1e3
+    kname = KERNEL_NAMES.get(info["config"]["kernel"], "?")
     achieved = alg_bytes / kern_avg / 1e9
 
     # self-measured write-only bandwidth (fill of the output buffer)
@@ -312,7 +322,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": desc, "numbers_per_step_per_gpu": total, "format": "u32",
+            "config": {"workload": desc, "numbers_per_step_per_gpu": total, "format": args.format,
                        "parallelism": "independent streams per GPU" if world > 1 else "1 GPU",
                        "l2": "20 GB written per step (> 129 MB L2) plus a 256 MiB rewrite "
                              "between timed steps",
@@ -321,11 +331,12 @@ def run_ours(args, rank, world, local_rank):
                        "resident_ctas_per_sm": info["resident_ctas_per_sm"],
                        "autotuned": tuned is not None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(),
+                         "frac": achieved / peak, "traffic": recorded_traffic(kname, args.workload),
                          "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_src == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel_ms_avg": 1e3 * kern_avg, "kernel": "mtgp_fast_kernel"},
+                         "kernel_ms_avg": 1e3 * kern_avg,
+                         "kernel": kname},
             "write_only_fill_gbs": write_gbs,
             "clocks": clk,
             "e2e": e2e,
@@ -339,14 +350,14 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def spot_check(w, counts, out, states0):
+def spot_check(w, counts, out, states0, fmt):
     """Whole outputs of a few streams of the first launch vs the oracle."""
     import oracle
     p = oracle.params_generate(w["mexp"], workloads.PARAM_SEED)
     offs = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
-    pick = [int(np.argmax(counts)), 0, counts.size - 1, counts.size // 2]
+    pick = sorted({int(np.argmax(counts)), 0, counts.size - 1, counts.size // 2})
     for s in pick:
-        ref, _ = oracle.generate(p, states0[s], int(counts[s]))
+        ref, _ = oracle.generate(p, states0[s], int(counts[s]), fmt)
         got = out[int(offs[s]):int(offs[s + 1])].cpu().numpy().view(np.uint32)
         if not np.array_equal(ref, got):
             return False
@@ -360,10 +371,11 @@ def measure_e2e(mtgp, torch, st, ids, counts, stream, args):
     except RuntimeError as e:
         return {"value": None, "unit": UNIT, "error": "pinned host buffer: %s" % str(e)[:120]}
     h2d = ids.nbytes + counts.nbytes
-    mtgp.mtgp_generate_to_host(st, ids, counts, mtgp.MTGP_U32, host, 0, stream)   # warm-up
+    fmt = FORMATS[args.format]
+    mtgp.mtgp_generate_to_host(st, ids, counts, fmt, host, 0, stream)   # warm-up
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        mtgp.mtgp_generate_to_host(st, ids, counts, mtgp.MTGP_U32, host, 0, stream)
+        mtgp.mtgp_generate_to_host(st, ids, counts, fmt, host, 0, stream)
     dt = time.perf_counter() - t0
     return {"value": total * args.e2e_steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4 * total,
@@ -400,7 +412,9 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uneven")
+    ap.add_argument("--workload", default="uneven", help="uneven | single | equal | long23209 | long44497")
+    ap.add_argument("--format", default="u32", choices=sorted(FORMATS),
+                    help="u32, f12 (float32 [1,2)) or f01 (float32 [0,1))")
     ap.add_argument("--streams", type=int, default=0, help="equal workload: stream count")
     ap.add_argument("--count", type=int, default=0, help="equal workload: numbers per stream")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -408,7 +422,8 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the serving trace (0 = skip the serving measurement)")
     ap.add_argument("--config", default="",
-                    help="force warps_per_cta,words_per_lane,coop_percent[,ctas_per_sm] (skips autotuning)")
+                    help="force warps_per_cta,words_per_lane,coop_percent[,ctas_per_sm[,kernel]] "
+                         "(skips autotuning)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -75,6 +75,8 @@ CONFIGS = [
     dict(warps_per_cta=1, words_per_lane=4, kernel=0),
     dict(warps_per_cta=8, words_per_lane=8, kernel=0),
     dict(warps_per_cta=4, words_per_lane=8, kernel=1),
+    dict(warps_per_cta=8, words_per_lane=8, kernel=0, ctas_per_sm=1),
+    dict(warps_per_cta=4, words_per_lane=8, kernel=0, coop_percent=1),
 ]
 
 
@@ -102,8 +104,9 @@ def test_single_stream_2p20_bit_exact():
 # ---------------------------------------------------------------------------
 # ragged counts, duplicate streams, every kernel configuration
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "w%d_k%d_kern%d" % (
-    c["warps_per_cta"], c["words_per_lane"], c["kernel"]))
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "w%d_k%d_kern%d_cap%d_coop%d" % (
+    c["warps_per_cta"], c["words_per_lane"], c["kernel"], c.get("ctas_per_sm", 0),
+    c.get("coop_percent", 100)))
 @pytest.mark.parametrize("fmt", FMTS)
 def test_ragged_requests(cfg, fmt):
     gp, op = _both_params(11213)
@@ -175,8 +178,29 @@ def test_other_exponents(mexp):
     _assert_same(mtgp.mtgp_get_statuses(st), states)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("mexp", [9689, 11213, 19937, 21701, 23209, 44497])
+@pytest.mark.parametrize("pseed", [1, 2, 3])
+def test_parameter_sweep(kernel, mexp, pseed):
+    """Both kernels over several exponents (state sizes) and parameter seeds
+    (other pos, shifts and tables)."""
+    gp, op = _both_params(mexp, pseed)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(12, dtype=np.uint32))
+    mtgp.mtgp_set_launch_config(st, warps_per_cta=4, words_per_lane=8, kernel=kernel)
+    states = np.stack([oracle.init_state(op, s) for s in range(12)])
+    ids = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 3, 3], np.uint32)
+    counts = np.array([op.n * 7 + 13, 1, 63, 64, 65, op.n, op.n - 1, op.n + 1, 5000, 0, 2 * op.n,
+                       33333, 10, op.n * 3], np.uint64)
+    for fmt in FMTS:
+        out = _gpu_generate(st, ids, counts, fmt)
+        ref, states = oracle.generate_many(op, states, ids, counts, fmt, THREADS)
+        _assert_same(out, ref, "kernel %d mexp %d seed %d fmt %d" % (kernel, mexp, pseed, fmt))
+    _assert_same(mtgp.mtgp_get_statuses(st), states)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("mexp,n", [(23209, 727), (44497, 1392)])
-def test_literal_state_sizes(tmp_path, mexp, n):
+def test_literal_state_sizes(tmp_path, mexp, n, kernel):
     o0 = oracle.params_generate(mexp, workloads.PARAM_SEED)
     f = {"mexp": mexp, "pos": o0.pos, "sh1": o0.sh1, "sh2": o0.sh2,
          "rec_basis": list(o0.rec_basis), "tmp_basis": list(o0.tmp_basis)}
@@ -185,6 +209,7 @@ def test_literal_state_sizes(tmp_path, mexp, n):
                                    n=n, mask=o0.mask)
     assert op.n == n
     st = mtgp.mtgp_init_statuses(gp, np.arange(4, dtype=np.uint32))
+    mtgp.mtgp_set_launch_config(st, warps_per_cta=4, words_per_lane=8, kernel=kernel)
     states = np.stack([oracle.init_state(op, s) for s in range(4)])
     _assert_same(mtgp.mtgp_get_statuses(st), states, "init")
     ids = np.arange(4, dtype=np.uint32)
@@ -193,6 +218,34 @@ def test_literal_state_sizes(tmp_path, mexp, n):
         out = _gpu_generate(st, ids, counts, fmt)
         ref, states = oracle.generate_many(op, states, ids, counts, fmt, THREADS)
         _assert_same(out, ref)
+    _assert_same(mtgp.mtgp_get_statuses(st), states)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_output_pointer_only_4_byte_aligned(kernel):
+    """A caller may pass an output that is 4- but not 8-byte aligned (a view
+    one element into a buffer)."""
+    gp, op = _both_params(11213)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(6, dtype=np.uint32))
+    mtgp.mtgp_set_launch_config(st, warps_per_cta=4, words_per_lane=8, kernel=kernel)
+    states = np.stack([oracle.init_state(op, s) for s in range(6)])
+    ids = np.arange(6, dtype=np.uint32)
+    counts = np.array([op.n * 9, op.n * 9 + 1, 4000, 1, 777, op.n], np.uint64)
+    total = int(counts.sum())
+    for fmt in FMTS:
+        buf = torch.full((total + 2,), -1, dtype=torch.int32, device="cuda")
+        view = buf[1:1 + total]
+        assert view.data_ptr() % 8 == 4
+        if fmt == mtgp.MTGP_U32:
+            mtgp.mtgp_generate_u32(st, ids, counts, view)
+        else:
+            mtgp.mtgp_generate_f32(st, ids, counts, fmt, view)
+        torch.cuda.synchronize()
+        mtgp.mtgp_check(st)
+        got = buf.cpu().numpy().view(np.uint32)
+        ref, states = oracle.generate_many(op, states, ids, counts, fmt, THREADS)
+        _assert_same(got[1:1 + total], ref, "kernel %d fmt %d" % (kernel, fmt))
+        assert got[0] == 0xFFFFFFFF and got[total + 1] == 0xFFFFFFFF
     _assert_same(mtgp.mtgp_get_statuses(st), states)
 
 
