@@ -513,21 +513,23 @@ extern "C" mtgp_status mtgp_init_statuses(mtgp_params_t params, const uint32_t* 
 
 LaunchCfg mtgp::default_config(const KParams& P)
 {
+    // 8 warps per SM; 128-word software-pipelined steps when the parameter
+    // set allows them (N - pos >= 256), else 256-word steps, else 128.
     LaunchCfg c;
     c.warps_per_cta = 4;
-    c.ctas_per_sm = 0;
-    c.k = 8;
+    c.ctas_per_sm = 2;
+    c.k = 4;
     c.kernel = 0;
     c.coop_percent = 0;
-    if (!fast_supported(P, 8))
-        c.k = fast_supported(P, 4) ? 4 : 8;
+    if (P.n - P.pos < 256u || !fast_supported(P, 4))
+        c.k = fast_supported(P, 8) ? 8 : 4;
     return c;
 }
 
 uint32_t mtgp::coop_count(const Work& w, const Geometry& g, int coop_percent)
 {
-    if (g.kernel != 0 || coop_percent <= 0 || w.items.empty())
-        return 0;
+    if (g.kernel != 0 || coop_percent <= 0 || w.items.empty() || g.k < g.threads / 32)
+        return 0;   // (the CTA-wide phase needs k >= warps per CTA)
     const double slots = (double)g.grid * (double)(g.threads / 32);
     const double thr = (double)w.total / slots * (double)coop_percent / 100.0;
     uint32_t n = 0;
@@ -902,9 +904,12 @@ std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
         for (int cap : {2, 3, 4, 6, 0})
             add(2, k, cap, 0);
         add(8, k, 1, 0);
+        add(8, k, 2, 0);
         add(8, k, 0, 0);
-        add(4, k, 0, 100);
-        add(8, k, 1, 100);
+        if (k >= 4)
+            add(4, k, 0, 100);
+        if (k >= 8)
+            add(8, k, 1, 100);
     }
     if (v.empty()) {   // no register-resident instantiation: tune the ring kernel
         for (int w : {2, 4, 8}) {

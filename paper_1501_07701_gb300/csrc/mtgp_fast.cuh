@@ -135,11 +135,15 @@ __device__ __forceinline__ void slow_store(uint32_t ou, uint32_t of, uint64_t g,
 //
 // No warp-synchronous instruction is executed under a lane-dependent
 // condition: the write phase is lane-predicated and holds only stores.
+//
+// S, Sw and Q all point into the same shared row (and ow into `out`), so
+// none of them is __restrict__: the loads of one step must stay after the
+// stores of the previous one.
 // ===========================================================================
 template <int M, int K, int WG, int FMT, bool SLOW>
-__device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32_t* __restrict__ S,
-                                        uint32_t* __restrict__ Sw, uint32_t* __restrict__ ow,
-                                        const uint32_t* __restrict__ Q, const KParams& P,
+__device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32_t* S,
+                                        uint32_t* Sw, uint32_t* ow,
+                                        const uint32_t* Q, const KParams& P,
                                         uint32_t warp, uint32_t lane, const uint32_t* __restrict__ Tb,
                                         uint32_t last_lane, uint32_t n_valid, uint64_t row_g,
                                         const Segment* __restrict__ segs, uint32_t s_first,
@@ -223,6 +227,85 @@ __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32
     }
 }
 
+// ===========================================================================
+// nfull consecutive full rows of one request, single warp, software-pipelined
+// steps of W = 128 words (K = 4 sub-steps).
+//
+// When N - pos >= 2W, the loads of step s+1 never touch a word that step s
+// writes: word i+1 and the unwrapped pick-ups lie beyond step s's columns,
+// and a wrapped pick-up (mirror) of a column c < W(s+2) lands below
+// c + pos - N < Ws.  The same holds from the last step of a row to the first
+// step of the next (its pick-ups end below pos + W <= N - W, where the last
+// step begins at or above N - W).  So the loads of step s+1 are issued
+// before the stores of step s, and one __syncwarp per step (after the
+// stores) orders every store before the loads that read it two steps later.
+// The loads issued during a row's last step are those of step 0 (the same
+// addresses in every row); after the last row they are simply unused.
+// ===========================================================================
+template <int M, int FMT>
+__device__ __forceinline__ void gen_rows_pipelined(uint32_t (&r)[M], uint32_t* Sw, uint32_t* ow,
+                                                   const uint32_t* Q, const KParams& P, uint32_t lane,
+                                                   const uint32_t* __restrict__ Tb, uint32_t last_lane,
+                                                   uint32_t nfull)
+{
+    constexpr int K = 4;
+    constexpr int NS = (M + K - 1) / K;   // steps per row (>= 3 here)
+    const uint32_t N = P.n;
+    uint32_t x1[K], xp[K], xq[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        x1[i] = Sw[32 * i + 1];
+        xp[i] = Q[32 * i];
+        xq[i] = Q[32 * i - 1];
+    }
+    for (uint32_t q = 0; q < nfull; ++q, ow += N) {
+#pragma unroll
+        for (int st = 0; st < NS; ++st) {
+            const int s0 = st * K;
+            const int n0 = (st + 1 < NS) ? s0 + K : 0;   // next step (next row's first)
+            uint32_t y1[K], yp[K], yq[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                if (n0 + i < M) {
+                    y1[i] = Sw[32 * (n0 + i) + 1];
+                    yp[i] = Q[32 * (n0 + i)];
+                    yq[i] = Q[32 * (n0 + i) - 1];
+                }
+            }
+            uint32_t xn[K], o[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                if (s0 + i < M) {
+                    const uint32_t yy = (r[s0 + i] & P.mask) ^ x1[i];
+                    const uint32_t y = yy ^ (yy << P.sh1) ^ (xp[i] >> P.sh2);
+                    xn[i] = y ^ tbl(Tb, 0u, y);
+                    o[i] = temper_convert<FMT>(xn[i], temper_index(xq[i]), Tb);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int m = s0 + i;
+                if (m < M && (m + 1 < M || lane <= last_lane)) {
+                    r[m] = xn[i];
+                    Sw[32 * m] = xn[i];
+                    if (32u * (uint32_t)m < P.mirror)
+                        Sw[32 * m + N] = xn[i];
+                    __stcs(ow + 32 * m, o[i]);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                if (n0 + i < M) {
+                    x1[i] = y1[i];
+                    xp[i] = yp[i];
+                    xq[i] = yq[i];
+                }
+            }
+        }
+    }
+}
+
 // Advances one stream by the segments [s_begin, s_end) of the work table.
 // WG warps take part (WG = 1: this warp alone; WG = G: the whole CTA).
 template <int M, int K, int WG>
@@ -271,27 +354,51 @@ __device__ __forceinline__ void run_item(const KParams& P, uint32_t* __restrict_
     uint32_t s = s_begin;
     Segment sg = segs[s];
     uint64_t seg_end = sg.g_start + sg.count;
-    for (uint64_t row = 0; row < total; row += N) {
+    uint64_t row = 0;
+    while (row < total) {
         while (row >= seg_end) {
             sg = segs[++s];
             seg_end = sg.g_start + sg.count;
         }
-        const uint64_t left = total - row;
-        const uint32_t n_valid = left < (uint64_t)N ? (uint32_t)left : N;
-        if (n_valid == N && row + N <= seg_end) {
+        if (row + N <= seg_end) {
+            // The rows that lie wholly inside this request run back to back:
+            // per row only the output pointer moves.
+            const uint32_t nfull = (uint32_t)min((seg_end - row) / N, (uint64_t)0xFFFFFFFFu);
             uint32_t* ow = out + sg.out_off + (row - sg.g_start) + 32u * wk + lane;
-            if (sg.fmt == 0)
-                gen_row<M, K, WG, 0, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
-                                            segs, s, s_end, out);
-            else if (sg.fmt == 1)
-                gen_row<M, K, WG, 1, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
-                                            segs, s, s_end, out);
-            else
-                gen_row<M, K, WG, 2, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
-                                            segs, s, s_end, out);
+            bool piped = false;
+            if constexpr (K == 4 && WG == 1 && M >= 9) {
+                if (N - P.pos >= 256u) {
+                    if (sg.fmt == 0)
+                        gen_rows_pipelined<M, 0>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull);
+                    else if (sg.fmt == 1)
+                        gen_rows_pipelined<M, 1>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull);
+                    else
+                        gen_rows_pipelined<M, 2>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull);
+                    piped = true;
+                }
+            }
+            if (piped) {
+            } else if (sg.fmt == 0) {
+                for (uint32_t q = 0; q < nfull; ++q, ow += N)
+                    gen_row<M, K, WG, 0, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
+                                                segs, s, s_end, out);
+            } else if (sg.fmt == 1) {
+                for (uint32_t q = 0; q < nfull; ++q, ow += N)
+                    gen_row<M, K, WG, 1, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
+                                                segs, s, s_end, out);
+            } else {
+                for (uint32_t q = 0; q < nfull; ++q, ow += N)
+                    gen_row<M, K, WG, 2, false>(r, S, Sw, ow, Q, P, wk, lane, Tb, last_lane, N, row,
+                                                segs, s, s_end, out);
+            }
+            row += (uint64_t)nfull * N;
         } else {
+            // a row that crosses into the next request, or the partial last row
+            const uint64_t left = total - row;
+            const uint32_t n_valid = left < (uint64_t)N ? (uint32_t)left : N;
             gen_row<M, K, WG, 0, true>(r, S, Sw, nullptr, Q, P, wk, lane, Tb, last_lane, n_valid,
                                        row, segs, s, s_end, out);
+            row += N;
         }
     }
 
@@ -335,6 +442,11 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
     }
     __syncthreads();
 
+    // The CTA-wide phase splits each parallel step's K sub-steps over the G
+    // warps, so it exists only for K >= G; otherwise every item is a
+    // single-warp item.
+    const uint32_t first_single = (K >= G) ? n_coop : 0u;
+    if constexpr (K >= G) {
     for (;;) {
         if (threadIdx.x == 0)
             s_claim = atomicAdd(&counters[0], 1u);
@@ -355,12 +467,13 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
         if (trace && threadIdx.x == 0)
             trace_item(trace, it, t0, segs, w);
     }
+    }
 
     uint32_t* S = smem + warp * fast_smem_words(P.n, P.mirror);
     for (;;) {
         uint32_t it = 0;
         if (lane == 0)
-            it = n_coop + atomicAdd(&counters[1], 1u);
+            it = first_single + atomicAdd(&counters[1], 1u);
         it = __shfl_sync(MTGP_FULL, it, 0);
         if (it >= n_items)
             break;

@@ -13,11 +13,13 @@ const void* fast_ptr_group_a(int M, int K, int G)
     case (10 * 16 + 8) * 16 + 8: return (const void*)mtgp_fast_kernel<10, 8, 8>;
     case (10 * 16 + 4) * 16 + 2: return (const void*)mtgp_fast_kernel<10, 4, 2>;
     case (10 * 16 + 4) * 16 + 4: return (const void*)mtgp_fast_kernel<10, 4, 4>;
+    case (10 * 16 + 4) * 16 + 8: return (const void*)mtgp_fast_kernel<10, 4, 8>;
     case (11 * 16 + 8) * 16 + 2: return (const void*)mtgp_fast_kernel<11, 8, 2>;
     case (11 * 16 + 8) * 16 + 4: return (const void*)mtgp_fast_kernel<11, 8, 4>;
     case (11 * 16 + 8) * 16 + 8: return (const void*)mtgp_fast_kernel<11, 8, 8>;
     case (11 * 16 + 4) * 16 + 2: return (const void*)mtgp_fast_kernel<11, 4, 2>;
     case (11 * 16 + 4) * 16 + 4: return (const void*)mtgp_fast_kernel<11, 4, 4>;
+    case (11 * 16 + 4) * 16 + 8: return (const void*)mtgp_fast_kernel<11, 4, 8>;
     default: return nullptr;
     }
 }

@@ -13,6 +13,7 @@ const void* fast_ptr_group_c(int M, int K, int G)
     case (44 * 16 + 8) * 16 + 8: return (const void*)mtgp_fast_kernel<44, 8, 8>;
     case (44 * 16 + 4) * 16 + 2: return (const void*)mtgp_fast_kernel<44, 4, 2>;
     case (44 * 16 + 4) * 16 + 4: return (const void*)mtgp_fast_kernel<44, 4, 4>;
+    case (44 * 16 + 4) * 16 + 8: return (const void*)mtgp_fast_kernel<44, 4, 8>;
     default: return nullptr;
     }
 }

@@ -185,7 +185,7 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
     int kernel = cfg.kernel;
     int warps = std::max(1, std::min(8, cfg.warps_per_cta));
     if (kernel == 0) {
-        // register-resident kernel: G in {2, 4, 8} (8 only with k = 8)
+        // register-resident kernel: G in {2, 4, 8}
         warps = warps <= 2 ? 2 : (warps <= 4 ? 4 : 8);
         if (!fast_supported(P, k, warps)) {
             if (fast_supported(P, 4, std::min(warps, 4))) {

@@ -166,7 +166,7 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
         return s;
     // Longest streams to whole CTAs, as in the ordinary path.
     uint32_t n_coop = 0;
-    if (g.kernel == 0 && st->cfg.coop_percent > 0) {
+    if (g.kernel == 0 && st->cfg.coop_percent > 0 && g.k >= g.threads / 32) {
         const double slots = (double)g.grid * (double)(g.threads / 32);
         const double thr = (double)total / slots * (double)st->cfg.coop_percent / 100.0;
         while (n_coop < n_items && (double)T.item_total[n_coop] >= thr)

@@ -76,6 +76,8 @@ CONFIGS = [
     dict(warps_per_cta=8, words_per_lane=8, kernel=0),
     dict(warps_per_cta=4, words_per_lane=8, kernel=1),
     dict(warps_per_cta=8, words_per_lane=8, kernel=0, ctas_per_sm=1),
+    dict(warps_per_cta=8, words_per_lane=4, kernel=0, ctas_per_sm=1),
+    dict(warps_per_cta=2, words_per_lane=4, kernel=0, ctas_per_sm=4),
     dict(warps_per_cta=4, words_per_lane=8, kernel=0, coop_percent=1),
 ]
 
@@ -218,6 +220,32 @@ def test_literal_state_sizes(tmp_path, mexp, n, kernel):
         out = _gpu_generate(st, ids, counts, fmt)
         ref, states = oracle.generate_many(op, states, ids, counts, fmt, THREADS)
         _assert_same(out, ref)
+    _assert_same(mtgp.mtgp_get_statuses(st), states)
+
+
+@pytest.mark.parametrize("mexp", [11213, 23209])
+@pytest.mark.parametrize("gap", [256, 255, 129])
+@pytest.mark.parametrize("warps", [2, 8])
+def test_step_width_boundaries(tmp_path, mexp, gap, warps):
+    """pos = N - gap with 128-word steps: gap >= 256 takes the software-
+    pipelined row loop (next step's loads before this step's stores), a
+    smaller gap the row-by-row loop.  Multi-request items and every format."""
+    o0 = oracle.params_generate(mexp, 7)
+    n = mexp // 32 + 1
+    f = {"mexp": mexp, "pos": n - gap, "sh1": o0.sh1, "sh2": o0.sh2,
+         "rec_basis": list(o0.rec_basis), "tmp_basis": list(o0.tmp_basis)}
+    gp = mtgp.mtgp_params_load(_params_file(tmp_path, f))
+    op = oracle.params_from_fields(mexp, n - gap, o0.sh1, o0.sh2, f["rec_basis"], f["tmp_basis"])
+    st = mtgp.mtgp_init_statuses(gp, np.arange(9, dtype=np.uint32))
+    mtgp.mtgp_set_launch_config(st, warps_per_cta=warps, words_per_lane=4, kernel=0, coop_percent=0)
+    states = np.stack([oracle.init_state(op, s) for s in range(9)])
+    ids = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 0, 0, 5], np.uint32)
+    counts = np.array([n * 40, n * 40 + 7, 1, n, n - 1, 2 * n + 1, 100000, 3, 0, n * 3, 17, n * 5],
+                      np.uint64)
+    for fmt in FMTS:
+        out = _gpu_generate(st, ids, counts, fmt)
+        ref, states = oracle.generate_many(op, states, ids, counts, fmt, THREADS)
+        _assert_same(out, ref, "gap %d warps %d fmt %d" % (gap, warps, fmt))
     _assert_same(mtgp.mtgp_get_statuses(st), states)
 
 
