@@ -69,7 +69,7 @@ def recorded_traffic(kernel: str, workload_name: str):
     return float(m_b.group(1))
 
 
-def workload(name: str, rank: int, streams: int = 0, count: int = 0):
+def workload(name: str, rank: int, streams: int = 0, count: int = 0, param_sets: int = 0):
     if name == "uneven":
         w = workloads.uneven()
         desc = ("uneven: 10000 MTGP32 Mexp 11213 streams, counts floor(2^U), U~U[10,22] "
@@ -89,7 +89,28 @@ def workload(name: str, rank: int, streams: int = 0, count: int = 0):
     else:
         raise SystemExit("unknown workload " + name)
     w["seeds"] = mdist.weak_seeds(w["seeds"], rank)
+    w["param_seeds"] = None
+    if param_sets:
+        n_sets = min(param_sets, w["seeds"].size)
+        w["param_seeds"] = workloads.param_seeds(w["seeds"].size, n_sets)
+        desc += "; %d parameter sets, stream s uses set s mod %d" % (n_sets, n_sets)
     return w, desc
+
+
+def oracle_params_of(w):
+    """Oracle parameter set of every stream (one shared set, or per stream)."""
+    import oracle
+    if w.get("param_seeds") is None:
+        p = oracle.params_generate(w["mexp"], workloads.PARAM_SEED)
+        return lambda s: p
+    cache = {}
+
+    def get(s):
+        k = int(w["param_seeds"][s])
+        if k not in cache:
+            cache[k] = oracle.params_generate(w["mexp"], k)
+        return cache[k]
+    return get
 
 
 class ClockSampler:
@@ -149,7 +170,10 @@ def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 26, seed=0):
     oracle time have been spent.  Returns (numbers/s, numbers, seconds,
     streams)."""
     import oracle
-    p = oracle.params_generate(w["mexp"], workloads.PARAM_SEED)
+    from concurrent.futures import ThreadPoolExecutor
+    p_of = oracle_params_of(w)
+    per_stream = w.get("param_seeds") is not None
+    pool = ThreadPoolExecutor(threads) if per_stream else None
     order = np.random.default_rng(seed).permutation(w["seeds"].size)
     done, t_all, used, k = 0, 0.0, 0, 0
     while t_all < budget_s and k < order.size:
@@ -159,12 +183,19 @@ def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 26, seed=0):
             batch.append(int(order[k]))
             acc += int(w["counts"][order[k]])
             k += 1
-        states = np.stack([oracle.init_state(p, int(w["seeds"][i])) for i in batch])
+        states = [oracle.init_state(p_of(i), int(w["seeds"][i])) for i in batch]
         t0 = time.perf_counter()
-        oracle.generate_many(p, states, np.arange(len(batch)), w["counts"][batch], 0, threads)
+        if per_stream:   # each stream with its own set, streams spread over the host threads
+            list(pool.map(lambda a: oracle.generate(p_of(a[0]), a[1], int(w["counts"][a[0]])),
+                          zip(batch, states)))
+        else:
+            oracle.generate_many(p_of(0), np.stack(states), np.arange(len(batch)), w["counts"][batch],
+                                 0, threads)
         t_all += time.perf_counter() - t0
         done += acc
         used += len(batch)
+    if pool:
+        pool.shutdown()
     return done / t_all, done, t_all, used
 
 
@@ -172,7 +203,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    w, desc = workload(args.workload, 0)
+    w, desc = workload(args.workload, 0, args.streams, args.count, args.param_sets)
     # each step: a bounded sample sized so the whole run stays within ~2 minutes
     per_step = min(10.0, max(0.05, 100.0 / max(1, args.steps + args.warmup)))
     vals, secs, nums = [], [], []
@@ -209,12 +240,17 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w, desc = workload(args.workload, rank, args.streams, args.count)
+    w, desc = workload(args.workload, rank, args.streams, args.count, args.param_sets)
     counts = w["counts"]
     total = int(counts.sum())
     stream = torch.cuda.Stream()
-    params = mtgp.mtgp_params_generate(w["mexp"], workloads.PARAM_SEED)
-    st = mtgp.mtgp_init_statuses(params, w["seeds"], stream)
+    if w["param_seeds"] is None:
+        params = mtgp.mtgp_params_generate(w["mexp"], workloads.PARAM_SEED)
+        st = mtgp.mtgp_init_statuses(params, w["seeds"], stream)
+    else:
+        uniq, set_of = np.unique(w["param_seeds"], return_inverse=True)
+        sets = [mtgp.mtgp_params_generate(w["mexp"], int(k)) for k in uniq]
+        st = mtgp.mtgp_init_statuses_multi(sets, set_of.astype(np.uint32), w["seeds"], stream)
     out = torch.empty(total, dtype=torch.int32, device=dev)
     ids = np.arange(w["seeds"].size, dtype=np.uint32)
     if args.config:
@@ -353,11 +389,11 @@ def run_ours(args, rank, world, local_rank):
 def spot_check(w, counts, out, states0, fmt):
     """Whole outputs of a few streams of the first launch vs the oracle."""
     import oracle
-    p = oracle.params_generate(w["mexp"], workloads.PARAM_SEED)
+    p_of = oracle_params_of(w)
     offs = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
     pick = sorted({int(np.argmax(counts)), 0, counts.size - 1, counts.size // 2})
     for s in pick:
-        ref, _ = oracle.generate(p, states0[s], int(counts[s]), fmt)
+        ref, _ = oracle.generate(p_of(s), states0[s], int(counts[s]), fmt)
         got = out[int(offs[s]):int(offs[s + 1])].cpu().numpy().view(np.uint32)
         if not np.array_equal(ref, got):
             return False
@@ -417,6 +453,9 @@ def main():
                     help="u32, f12 (float32 [1,2)) or f01 (float32 [0,1))")
     ap.add_argument("--streams", type=int, default=0, help="equal workload: stream count")
     ap.add_argument("--count", type=int, default=0, help="equal workload: numbers per stream")
+    ap.add_argument("--param-sets", type=int, default=0,
+                    help="one parameter set per stream group: K distinct sets, stream s uses set "
+                         "s mod K (0 = one shared set)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--serving-seconds", type=float, default=10.0,

@@ -122,6 +122,21 @@ mtgp_status mtgp_params_free(mtgp_params_t params);
 mtgp_status mtgp_init_statuses(mtgp_params_t params, const uint32_t* seeds, uint32_t n_streams,
                                void* cuda_stream, mtgp_streams_t* out);
 
+/* Sec. 3.1 / Sec. 4.1 / Sec. 5.1: one parameterized status per stream (the
+ * paper's 10 000 independent parameter sets, and its "Random Spacing" pairs
+ * of parameterized and seed statuses).  Stream s uses the parameter set
+ * sets[set_of_stream[s]] and is seeded from seeds[s] as in
+ * mtgp_init_statuses.  All n_sets sets must share Mexp (hence N and the
+ * mask); they may differ in pos, sh1, sh2 and the tables.  `sets`,
+ * `set_of_stream` (n_streams indices < n_sets) and `seeds` are host arrays
+ * read before the call returns; the parameter handles are copied.  The
+ * resulting handle works with every generation, plan, serving, checkpoint
+ * and tuning call.  MTGP_EINVAL if the sets differ in Mexp/N or an index is
+ * out of range. */
+mtgp_status mtgp_init_statuses_multi(const mtgp_params_t* sets, uint32_t n_sets,
+                                     const uint32_t* set_of_stream, const uint32_t* seeds,
+                                     uint32_t n_streams, void* cuda_stream, mtgp_streams_t* out);
+
 /* Overwrites all states from the host array `states` (n_streams x N words,
  * row s = stream s, oldest word first).  Synchronous. */
 mtgp_status mtgp_set_statuses(mtgp_streams_t streams, const uint32_t* states, void* cuda_stream);

@@ -449,6 +449,10 @@ static void destroy_streams(mtgp_streams* h)
         cudaFree(h->d_states);
     if (h->d_err)
         cudaFree(h->d_err);
+    if (h->d_sets)
+        cudaFree(h->d_sets);
+    if (h->d_set_of)
+        cudaFree(h->d_set_of);
     delete h;
 }
 
@@ -506,6 +510,73 @@ extern "C" mtgp_status mtgp_init_statuses(mtgp_params_t params, const uint32_t* 
         return bail(e, "init kernel launch");
     // pageable seeds: the copy above is complete when cudaMemcpyAsync returns
     h->cfg = default_config(h->P.k);
+    *out = h;
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_init_statuses_multi(const mtgp_params_t* sets, uint32_t n_sets,
+                                                const uint32_t* set_of_stream, const uint32_t* seeds,
+                                                uint32_t n_streams, void* cuda_stream,
+                                                mtgp_streams_t* out)
+{
+    GUARD_BEGIN
+    if (!sets || !set_of_stream || !seeds || !out)
+        return fail(MTGP_EINVAL, "null argument");
+    if (n_sets == 0 || n_streams == 0)
+        return fail(MTGP_EINVAL, "n_sets and n_streams must be >= 1");
+    for (uint32_t i = 0; i < n_sets; ++i) {
+        if (!sets[i])
+            return fail(MTGP_EINVAL, "parameter set %u is null", i);
+        if (sets[i]->d.mexp != sets[0]->d.mexp || sets[i]->d.n != sets[0]->d.n ||
+            sets[i]->d.mask != sets[0]->d.mask)
+            return fail(MTGP_EINVAL, "parameter set %u: Mexp/N/mask differ from set 0 (all sets of a "
+                        "handle share the state size)", i);
+    }
+    for (uint32_t s = 0; s < n_streams; ++s)
+        if (set_of_stream[s] >= n_sets)
+            return fail(MTGP_EINVAL, "stream %u: parameter set %u out of range (n_sets = %u)", s,
+                        set_of_stream[s], n_sets);
+    // Representative set for everything decided per launch (step width,
+    // shared-memory mirror): the largest pos and mirror of all sets.
+    mtgp_params rep = *sets[0];
+    std::vector<KSet> ks(n_sets);
+    for (uint32_t i = 0; i < n_sets; ++i) {
+        const KParams& k = sets[i]->k;
+        rep.k.pos = std::max(rep.k.pos, k.pos);
+        rep.k.mirror = std::max(rep.k.mirror, k.mirror);
+        ks[i].pos = k.pos;
+        ks[i].sh1 = k.sh1;
+        ks[i].sh2 = k.sh2;
+        ks[i].mirror = k.mirror;
+        for (int j = 0; j < 16; ++j) {
+            ks[i].rec[j] = k.rec[j];
+            ks[i].tmp[j] = k.tmp[j];
+            ks[i].flt[j] = k.flt[j];
+        }
+    }
+    rep.d.pos = rep.k.pos;
+    mtgp_streams_t h = nullptr;
+    mtgp_status st = mtgp_init_statuses(&rep, seeds, n_streams, cuda_stream, &h);
+    if (st != MTGP_OK)
+        return st;
+    DeviceGuard g(h->device);
+    cudaStream_t cs = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMalloc(&h->d_sets, ks.size() * sizeof(KSet));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&h->d_set_of, (size_t)n_streams * sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_sets, ks.data(), ks.size() * sizeof(KSet), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_set_of, set_of_stream, (size_t)n_streams * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(cs);   // ks is a local vector
+    if (e != cudaSuccess) {
+        destroy_streams(h);
+        return fail_cuda(e, "per-stream parameter sets");
+    }
+    h->n_sets = n_sets;
     *out = h;
     return ok();
     GUARD_END
@@ -653,11 +724,13 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
     a.items = (const WorkItem*)((char*)sl.dev + io);
     a.segs = (const Segment*)((char*)sl.dev + so);
     a.n_items = (uint32_t)w.items.size();
-    a.n_coop = coop_count(w, g, cfg.coop_percent);
+    a.n_coop = st->d_sets ? 0u : coop_count(w, g, cfg.coop_percent);
     a.counter = (uint32_t*)sl.dev;
     a.out = (uint32_t*)out;
     a.err = st->d_err;
     a.trace = nullptr;
+    a.sets = st->d_sets;
+    a.set_of = st->d_set_of;
     CUDA_TRY(launch_generate(a, g, s), "generation kernel launch");
     CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
     sl.ev_recorded = true;
@@ -1072,12 +1145,14 @@ static mtgp_status record_graph(mtgp_plan* p)
     a.items = (const WorkItem*)((char*)p->d_table + p->items_off);
     a.segs = (const Segment*)((char*)p->d_table + p->segs_off);
     a.n_items = p->n_items;
-    a.n_coop = coop_count(p->work, p->geo, p->cfg.coop_percent);
+    a.n_coop = p->st->d_sets ? 0u : coop_count(p->work, p->geo, p->cfg.coop_percent);
     p->n_coop = a.n_coop;
     a.counter = (uint32_t*)p->d_table;
     a.out = (uint32_t*)p->out;
     a.err = p->st->d_err;
     a.trace = p->d_trace;
+    a.sets = p->st->d_sets;
+    a.set_of = p->st->d_set_of;
     cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, p->geo, cap) : e1;
     cudaGraph_t graph = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(cap, &graph);

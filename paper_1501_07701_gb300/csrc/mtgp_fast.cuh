@@ -74,6 +74,13 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Per-stream scalars the row code reads: the handle's parameter set, or the
+// stream's own set when the handle has one per stream (all sets of a handle
+// share N and the mask).  Kept in registers for the whole item.
+struct RowP {
+    uint32_t n, mask, pos, sh1, sh2, mirror;
+};
+
 // Tables in shared memory: 16 words each, at a 64-byte aligned base, so
 // that entry k of a table sits in bank k and any lookup pattern of a warp is
 // one conflict-free wavefront.  Tb[0..16) recursion, Tb[16..32) tempering,
@@ -143,7 +150,7 @@ __device__ __forceinline__ void slow_store(uint32_t ou, uint32_t of, uint64_t g,
 template <int M, int K, int WG, int FMT, bool SLOW>
 __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32_t* S,
                                         uint32_t* Sw, uint32_t* ow,
-                                        const uint32_t* Q, const KParams& P,
+                                        const uint32_t* Q, const RowP& P,
                                         uint32_t warp, uint32_t lane, const uint32_t* __restrict__ Tb,
                                         uint32_t last_lane, uint32_t n_valid, uint64_t row_g,
                                         const Segment* __restrict__ segs, uint32_t s_first,
@@ -244,7 +251,7 @@ __device__ __forceinline__ void gen_row(uint32_t (&r)[(M + WG - 1) / WG], uint32
 // ===========================================================================
 template <int M, int FMT>
 __device__ __forceinline__ void gen_rows_pipelined(uint32_t (&r)[M], uint32_t* Sw, uint32_t* ow,
-                                                   const uint32_t* Q, const KParams& P, uint32_t lane,
+                                                   const uint32_t* Q, const RowP& P, uint32_t lane,
                                                    const uint32_t* __restrict__ Tb, uint32_t last_lane,
                                                    uint32_t nfull)
 {
@@ -309,10 +316,10 @@ __device__ __forceinline__ void gen_rows_pipelined(uint32_t (&r)[M], uint32_t* S
 // Advances one stream by the segments [s_begin, s_end) of the work table.
 // WG warps take part (WG = 1: this warp alone; WG = G: the whole CTA).
 template <int M, int K, int WG>
-__device__ __forceinline__ void run_item(const KParams& P, uint32_t* __restrict__ g, uint32_t* __restrict__ S,
-                                         const Segment* __restrict__ segs, uint32_t s_begin,
-                                         uint32_t s_end, uint32_t* __restrict__ out, uint32_t warp,
-                                         uint32_t lane, const uint32_t* __restrict__ Tb)
+__device__ __forceinline__ void run_item(const KParams& KP, const RowP& P, uint32_t* __restrict__ g,
+                                         uint32_t* __restrict__ S, const Segment* __restrict__ segs,
+                                         uint32_t s_begin, uint32_t s_end, uint32_t* __restrict__ out,
+                                         uint32_t warp, uint32_t lane, const uint32_t* __restrict__ Tb)
 {
     constexpr int J = (M + WG - 1) / WG;
     const uint32_t N = P.n;
@@ -321,7 +328,7 @@ __device__ __forceinline__ void run_item(const KParams& P, uint32_t* __restrict_
     const uint32_t last_lane = (N - 1u) & 31u;   // lane of column N-1 (group M-1)
 
     // stage in: the state row (HBM) -> S through 16-byte cp.async
-    for (uint32_t c = tid; c < (P.np >> 2); c += 32u * WG)
+    for (uint32_t c = tid; c < (KP.np >> 2); c += 32u * WG)
         cp_async16(S + 4u * c, g + 4u * c);
     cp_async_wait_all();
     if (WG > 1)
@@ -428,26 +435,32 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
                                                            uint32_t n_items, uint32_t n_coop,
                                                            uint32_t* __restrict__ counters,
                                                            uint32_t* __restrict__ out, int* __restrict__ err,
-                                                           uint64_t* __restrict__ trace)
+                                                           uint64_t* __restrict__ trace,
+                                                           const KSet* __restrict__ sets,
+                                                           const uint32_t* __restrict__ set_of)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_claim;
-    __shared__ __align__(64) uint32_t Tb[48];
+    // Tables: Tb[0] holds the handle's set; with per-stream sets each warp
+    // loads its stream's tables into its own Tb[warp] (192-byte rows, so
+    // every table starts on a 64-byte boundary: entry k in bank k).
+    __shared__ __align__(64) uint32_t Tb[G][48];
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
     if (threadIdx.x < 16) {
-        Tb[threadIdx.x] = P.rec[threadIdx.x];
-        Tb[16 + threadIdx.x] = P.tmp[threadIdx.x];
-        Tb[32 + threadIdx.x] = P.flt[threadIdx.x];
+        Tb[0][threadIdx.x] = P.rec[threadIdx.x];
+        Tb[0][16 + threadIdx.x] = P.tmp[threadIdx.x];
+        Tb[0][32 + threadIdx.x] = P.flt[threadIdx.x];
     }
     __syncthreads();
+    const RowP R0 = {P.n, P.mask, P.pos, P.sh1, P.sh2, P.mirror};
 
     // The CTA-wide phase splits each parallel step's K sub-steps over the G
-    // warps, so it exists only for K >= G; otherwise every item is a
-    // single-warp item.
-    const uint32_t first_single = (K >= G) ? n_coop : 0u;
+    // warps, so it exists only for K >= G and for handles with one parameter
+    // set; otherwise every item is a single-warp item.
+    const uint32_t first_single = (K >= G && !sets) ? n_coop : 0u;
     if constexpr (K >= G) {
-    for (;;) {
+    for (; !sets;) {
         if (threadIdx.x == 0)
             s_claim = atomicAdd(&counters[0], 1u);
         __syncthreads();
@@ -462,8 +475,8 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
             continue;
         }
         const uint64_t t0 = trace ? global_ns() : 0;
-        run_item<M, K, G>(P, states + (size_t)w.stream * P.np, smem, segs, w.seg_begin,
-                          w.seg_begin + w.nseg, out, warp, lane, Tb);
+        run_item<M, K, G>(P, R0, states + (size_t)w.stream * P.np, smem, segs, w.seg_begin,
+                          w.seg_begin + w.nseg, out, warp, lane, Tb[0]);
         if (trace && threadIdx.x == 0)
             trace_item(trace, it, t0, segs, w);
     }
@@ -484,8 +497,22 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
             continue;
         }
         const uint64_t t0 = trace ? global_ns() : 0;
-        run_item<M, K, 1>(P, states + (size_t)w.stream * P.np, S, segs, w.seg_begin,
-                          w.seg_begin + w.nseg, out, warp, lane, Tb);
+        if (sets) {
+            // this stream's own parameter set
+            const KSet& ks = sets[set_of[w.stream]];
+            const RowP R = {P.n, P.mask, ks.pos, ks.sh1, ks.sh2, ks.mirror};
+            if (lane < 16u) {
+                Tb[warp][lane] = ks.rec[lane];
+                Tb[warp][16u + lane] = ks.tmp[lane];
+                Tb[warp][32u + lane] = ks.flt[lane];
+            }
+            __syncwarp();
+            run_item<M, K, 1>(P, R, states + (size_t)w.stream * P.np, S, segs, w.seg_begin,
+                              w.seg_begin + w.nseg, out, warp, lane, Tb[warp]);
+        } else {
+            run_item<M, K, 1>(P, R0, states + (size_t)w.stream * P.np, S, segs, w.seg_begin,
+                              w.seg_begin + w.nseg, out, warp, lane, Tb[0]);
+        }
         if (trace && lane == 0)
             trace_item(trace, it, t0, segs, w);
     }

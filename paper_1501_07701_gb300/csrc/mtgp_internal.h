@@ -22,6 +22,18 @@ struct KParams {
     uint32_t flt[16];
 };
 
+// One parameter set of a handle whose streams do not all share the handle's
+// set (per-stream parameter sets, the paper's setting of one parameterized
+// status per stream).  All sets of a handle have the same Mexp, hence the same
+// N and mask; the kernels read pos, the shifts, the mirror width and the three
+// tables per stream from here.
+struct KSet {
+    uint32_t pos, sh1, sh2, mirror;
+    uint32_t rec[16];
+    uint32_t tmp[16];
+    uint32_t flt[16];
+};
+
 // One stream touched by a launch.  Its requests are the segments
 // [seg_begin, seg_begin + nseg); they are generated back to back, so the
 // stream's output index g runs over 0 .. total-1 across its segments.
@@ -55,12 +67,13 @@ struct LaunchCfg {
 // Per-warp shared-memory footprint (32-bit words).
 //   fast: S[0 .. N + mirror) rounded up to 4 words (16-byte aligned rows for
 //         the cp.async stage-in).
-//   ring: S[0 .. N) rounded up to 4 words.
+//   ring: the warp's REC/TMP tables (32 words), then S[0 .. N) rounded up
+//         to 4 words.
 __host__ __device__ inline uint32_t fast_smem_words(uint32_t n, uint32_t mirror)
 {
     return (n + mirror + 3u) & ~3u;
 }
-__host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return (n + 3u) & ~3u; }
+__host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return 32u + ((n + 3u) & ~3u); }
 
 // True if the register-resident kernel has an instantiation for this N, k
 // and g warps per CTA, the window 32*k fits (32*k <= N - pos), and the
@@ -83,6 +96,8 @@ struct GenArgs {
     uint32_t* out;
     int* err;
     uint64_t* trace;     // optional: 4 words per item (start ns, end ns, SM, numbers)
+    const KSet* sets = nullptr;        // per-stream parameter sets (null: every stream uses P)
+    const uint32_t* set_of = nullptr;  // set index of each stream when `sets` is given
 };
 
 // Resolved launch geometry for a configuration.

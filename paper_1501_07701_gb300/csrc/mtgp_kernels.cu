@@ -70,21 +70,18 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
                                                         const WorkItem* __restrict__ items,
                                                         const Segment* __restrict__ segs,
                                                         uint32_t n_items, uint32_t* __restrict__ counter,
-                                                        uint32_t* __restrict__ out, int* __restrict__ err)
+                                                        uint32_t* __restrict__ out, int* __restrict__ err,
+                                                        const KSet* __restrict__ sets,
+                                                        const uint32_t* __restrict__ set_of)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t* rec = smem;
-    uint32_t* tmp = smem + 16;
-    if (threadIdx.x < 16) {
-        rec[threadIdx.x] = P.rec[threadIdx.x];
-        tmp[threadIdx.x] = P.tmp[threadIdx.x];
-    }
-    __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t N = P.n, pos = P.pos;
-    uint32_t* S = smem + 32 + warp * ring_smem_words(N);
-    const uint32_t Wc = (N - pos) < 32u ? (N - pos) : 32u;
+    const uint32_t N = P.n;
+    // per warp: REC[16], TMP[16], then the state row
+    uint32_t* rec = smem + warp * ring_smem_words(N);
+    uint32_t* tmp = rec + 16;
+    uint32_t* S = rec + 32;
 
     for (;;) {
         uint32_t it = 0;
@@ -99,6 +96,22 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
                 atomicOr(err, 1);
             continue;
         }
+        // this stream's parameter set (the handle's own, or its per-stream set)
+        uint32_t pos = P.pos, sh1 = P.sh1, sh2 = P.sh2;
+        if (sets) {
+            const KSet& ks = sets[set_of[w.stream]];
+            pos = ks.pos;
+            sh1 = ks.sh1;
+            sh2 = ks.sh2;
+            if (lane < 16u) {
+                rec[lane] = ks.rec[lane];
+                tmp[lane] = ks.tmp[lane];
+            }
+        } else if (lane < 16u) {
+            rec[lane] = P.rec[lane];
+            tmp[lane] = P.tmp[lane];
+        }
+        const uint32_t Wc = (N - pos) < 32u ? (N - pos) : 32u;
         uint32_t* g = states + (size_t)w.stream * P.np;
         for (uint32_t j = lane; j < N; j += 32u)
             S[j] = g[j];
@@ -124,8 +137,8 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
                     uint32_t cq = c + pos - 1u;
                     cq = cq >= N ? cq - N : cq;
                     uint32_t y = (S[c] & P.mask) ^ S[c1];
-                    y ^= y << P.sh1;
-                    y ^= S[cp] >> P.sh2;
+                    y ^= y << sh1;
+                    y ^= S[cp] >> sh2;
                     xn = y ^ rec[y & 15u];
                     uint32_t t = S[cq];
                     t ^= t >> 16;
@@ -204,7 +217,7 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
         g->smem = (size_t)warps * fast_smem_words(P.n, P.mirror) * 4u;
         fn = fast_kernel_ptr(fast_m(P), k, warps);
     } else {
-        g->smem = (size_t)(32u + warps * ring_smem_words(P.n)) * 4u;
+        g->smem = (size_t)warps * ring_smem_words(P.n) * 4u;
         fn = (const void*)mtgp_ring_kernel;
     }
     cudaError_t e;
@@ -245,7 +258,8 @@ cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
         return launch_fast((int)((a.P.n + 31u) / 32u), g.k, g.threads / 32, a, dim3(g.grid),
                            dim3(g.threads), g.smem, s);
     mtgp_ring_kernel<<<g.grid, g.threads, g.smem, s>>>(a.P, a.states, a.n_streams, a.items, a.segs,
-                                                       a.n_items, a.counter, a.out, a.err);
+                                                       a.n_items, a.counter, a.out, a.err, a.sets,
+                                                       a.set_of);
     return cudaGetLastError();
 }
 
@@ -284,8 +298,10 @@ cudaError_t launch_fast(int M, int K, int G, const GenArgs& a, dim3 grid, dim3 b
     uint32_t* out = a.out;
     int* err = a.err;
     uint64_t* trace = a.trace;
+    const KSet* sets = a.sets;
+    const uint32_t* set_of = a.set_of;
     void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &n_coop, &counter, &out, &err,
-                    &trace};
+                    &trace, &sets, &set_of};
     return cudaLaunchKernel(fn, grid, block, args, smem, s);
 }
 

@@ -166,7 +166,7 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
         return s;
     // Longest streams to whole CTAs, as in the ordinary path.
     uint32_t n_coop = 0;
-    if (g.kernel == 0 && st->cfg.coop_percent > 0 && g.k >= g.threads / 32) {
+    if (g.kernel == 0 && st->cfg.coop_percent > 0 && g.k >= g.threads / 32 && !st->d_sets) {
         const double slots = (double)g.grid * (double)(g.threads / 32);
         const double thr = (double)total / slots * (double)st->cfg.coop_percent / 100.0;
         while (n_coop < n_items && (double)T.item_total[n_coop] >= thr)
@@ -193,6 +193,8 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
     a.out = (uint32_t*)out;
     a.err = st->d_err;
     a.trace = nullptr;
+    a.sets = st->d_sets;
+    a.set_of = st->d_set_of;
     e = launch_generate(a, g, cs);
     if (e != cudaSuccess)
         return fail_cuda(e, "generation kernel launch (no-alloc)");

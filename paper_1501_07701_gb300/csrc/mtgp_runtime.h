@@ -57,6 +57,12 @@ struct mtgp_streams {
     uint32_t n_streams = 0;
     uint32_t* d_states = nullptr;   // n_streams rows of P.k.np words
     int* d_err = nullptr;           // device error word
+    // per-stream parameter sets (mtgp_init_statuses_multi): then P is a
+    // representative set (largest pos and mirror, for window checks and
+    // shared-memory sizing) and the kernels read each stream's own set
+    mtgp::KSet* d_sets = nullptr;
+    uint32_t* d_set_of = nullptr;
+    uint32_t n_sets = 0;
     mtgp::LaunchCfg cfg{};
     std::array<mtgp::TableSlot, 4> slots{};
     int next_slot = 0;

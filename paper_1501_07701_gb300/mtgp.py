@@ -83,6 +83,8 @@ _SIGS = {
     "mtgp_params_get": [_VP, ctypes.POINTER(ParamsDesc)],
     "mtgp_params_free": [_VP],
     "mtgp_init_statuses": [_VP, _U32P, ctypes.c_uint32, _VP, ctypes.POINTER(_VP)],
+    "mtgp_init_statuses_multi": [ctypes.POINTER(_VP), ctypes.c_uint32, _U32P, _U32P, ctypes.c_uint32,
+                                 _VP, ctypes.POINTER(_VP)],
     "mtgp_set_statuses": [_VP, _U32P, _VP],
     "mtgp_get_statuses": [_VP, _U32P, _VP],
     "mtgp_streams_info": [_VP, _U32P, _U32P],
@@ -289,6 +291,19 @@ def mtgp_init_statuses(params: Params, seeds, stream=None) -> Streams:
     h = _VP()
     _call("mtgp_init_statuses", params.handle, _p32(seeds), seeds.size, _stream_handle(stream),
           ctypes.byref(h))
+    return Streams(h)
+
+
+def mtgp_init_statuses_multi(params_list, set_of_stream, seeds, stream=None) -> Streams:
+    """One parameter set per stream: stream s uses params_list[set_of_stream[s]]."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+    set_of = np.ascontiguousarray(set_of_stream, dtype=np.uint32)
+    if set_of.shape != seeds.shape:
+        raise ValueError("set_of_stream and seeds must have the same length")
+    arr = (_VP * len(params_list))(*[p.handle for p in params_list])
+    h = _VP()
+    _call("mtgp_init_statuses_multi", arr, len(params_list), _p32(set_of), _p32(seeds), seeds.size,
+          _stream_handle(stream), ctypes.byref(h))
     return Streams(h)
 
 

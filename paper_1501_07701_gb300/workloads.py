@@ -66,6 +66,12 @@ def serving_trace(duration_s: float = 10.0, rate: float = 50000.0, n_streams: in
     return {"t": t, "ids": ids, "counts": k, "fmt": fmt, "n_streams": n_streams}
 
 
+def param_seeds(n_streams: int, n_sets: int):
+    """Per-stream parameter-set seeds for the one-set-per-stream setting:
+    stream s uses the set generated from seed PARAM_SEED + 1 + (s mod n_sets)."""
+    return (PARAM_SEED + 1 + np.arange(n_streams) % n_sets).astype(np.uint64)
+
+
 def toy_fields(rng: np.random.Generator, n: int):
     """Random parameter fields for a toy status with N = n words (1 <= pos <= n-1)."""
     r = int(rng.integers(1, 32))
