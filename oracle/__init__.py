@@ -91,6 +91,10 @@ def _load():
             lib.omtgp_generate.argtypes = [P, u32p, ctypes.c_uint64, ctypes.c_int, u32p]
             lib.omtgp_generate_many.argtypes = [P, u32p, ctypes.c_uint32, u32p, u64p,
                                                 ctypes.c_uint32, ctypes.c_int, u32p, ctypes.c_int]
+            lib.omtgp_gap_histogram.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint, ctypes.c_uint,
+                                                ctypes.c_uint, u64p]
+            lib.omtgp_hamming_pairs.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint, ctypes.c_uint,
+                                                ctypes.c_uint, u32p, ctypes.c_uint, u64p]
             _lib = lib
     return _lib
 
@@ -150,3 +154,25 @@ def generate_many(p: Params, states: np.ndarray, ids, counts, fmt: int = U32,
     if rc != 0:
         raise RuntimeError("oracle: generate_many failed")
     return out[:total], st
+
+
+def gap_histogram(x, r: int = 25, b: int = 5, t: int = 128) -> np.ndarray:
+    """Gap-length histogram (Sec. 4.2, test 35): t + 1 counts."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    hist = np.zeros(t + 1, dtype=np.uint64)
+    if _load().omtgp_gap_histogram(_u32p(x), x.size, r, b, t, _u64p(hist)) != 0:
+        raise ValueError("oracle: bad gap-test arguments")
+    return hist
+
+
+def hamming_pairs(x, r: int = 25, s: int = 5, L: int = 1200, bounds=()) -> np.ndarray:
+    """Table of weight classes of successive block pairs (Sec. 4.2, test 100):
+    C x C counts, C = len(bounds) + 1."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    bnd = np.ascontiguousarray(bounds, dtype=np.uint32)
+    C = bnd.size + 1
+    table = np.zeros(C * C, dtype=np.uint64)
+    if _load().omtgp_hamming_pairs(_u32p(x), x.size, r, s, L, _u32p(bnd), bnd.size,
+                                   _u64p(table)) != 0:
+        raise ValueError("oracle: bad Hamming-test arguments")
+    return table.reshape(C, C)

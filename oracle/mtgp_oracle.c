@@ -244,3 +244,69 @@ int omtgp_generate_many(const omtgp_params* p, uint32_t* states,
     free(offs); free(jobs); free(th);
     return rc;
 }
+
+
+/* ========================================================================
+ * Test 35: gap-length histogram (Sec. 4.2).
+ * ======================================================================== */
+static int in_field_is_zero(uint32_t x, unsigned r, unsigned width)
+{
+    /* the `width` bits that follow the r dropped leading bits */
+    uint64_t v = ((uint64_t)x << r) & 0xFFFFFFFFull;   /* drop r leading bits */
+    return (v >> (32 - width)) == 0;
+}
+
+int omtgp_gap_histogram(const uint32_t* x, uint64_t n, unsigned r, unsigned b, unsigned t,
+                        uint64_t* hist)
+{
+    uint64_t j, run = 0;
+    unsigned s;
+    if (!hist || (n && !x) || b < 1 || r + b > 32 || t < 1)
+        return -1;
+    for (s = 0; s <= t; ++s)
+        hist[s] = 0;
+    for (j = 0; j < n; ++j) {
+        if (in_field_is_zero(x[j], r, b)) {      /* a visit ends the current gap */
+            hist[run < t ? run : t] += 1;
+            run = 0;
+        } else {
+            run += 1;
+        }
+    }
+    return 0;
+}
+
+/* ========================================================================
+ * Test 100: table of the weight classes of successive block pairs (Sec. 4.2).
+ * ======================================================================== */
+int omtgp_hamming_pairs(const uint32_t* x, uint64_t n, unsigned r, unsigned s, unsigned L,
+                        const uint32_t* bounds, unsigned n_bounds, uint64_t* table)
+{
+    const unsigned C = n_bounds + 1;
+    uint64_t j, per_block, n_blocks, k;
+    unsigned i, bit, cls[2] = {0, 0};
+    if (!table || (n && !x) || s < 1 || r + s > 32 || L == 0 || L % s != 0 ||
+        (n_bounds && !bounds))
+        return -1;
+    for (i = 0; i < C * C; ++i)
+        table[i] = 0;
+    per_block = L / s;
+    n_blocks = n / per_block;
+    n_blocks -= n_blocks % 2;                 /* complete pairs only */
+    for (k = 0; k < n_blocks; ++k) {
+        unsigned w = 0, c = 0;
+        for (j = k * per_block; j < (k + 1) * per_block; ++j) {
+            uint64_t v = ((uint64_t)x[j] << r) & 0xFFFFFFFFull;
+            uint32_t field = (uint32_t)(v >> (32 - s));   /* the s bits, MSB first */
+            for (bit = 0; bit < s; ++bit)
+                w += (field >> (s - 1 - bit)) & 1u;
+        }
+        for (i = 0; i < n_bounds; ++i)
+            if (bounds[i] <= w)
+                ++c;
+        cls[k % 2] = c;
+        if (k % 2 == 1)
+            table[cls[0] * C + cls[1]] += 1;
+    }
+    return 0;
+}

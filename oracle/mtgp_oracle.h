@@ -27,6 +27,13 @@
  *   omtgp_generate         pinned (hand-worked example, GF(2) bit-matrix
  *                          formulation, impulse responses, linearity,
  *                          linear complexity <= Mexp, float value identities)
+ *   omtgp_gap_histogram    pinned (constructed visit patterns with known
+ *                          gaps, bit-field selection, period-k closed form,
+ *                          length invariant, chi-square sanity on an
+ *                          independent generator)
+ *   omtgp_hamming_pairs    pinned (constant and alternating blocks, blocks
+ *                          of known weight against the class bounds, pair
+ *                          count, chi-square sanity)
  */
 #ifndef MTGP_ORACLE_H
 #define MTGP_ORACLE_H
@@ -80,6 +87,35 @@ int omtgp_generate_many(const omtgp_params* p, uint32_t* states,
                         uint32_t n_streams, const uint32_t* ids,
                         const uint64_t* counts, uint32_t n_req, int fmt,
                         uint32_t* out, int n_threads);
+
+/* ------------------------------------------------------------------------
+ * Statistics of the paper's two failing BigCrush tests (Sec. 4.2), restated
+ * from their definitions as plain sequential loops over 32-bit outputs.
+ * ------------------------------------------------------------------------ */
+
+/* Test 35 (Knuth's gap test; r = 25, alpha = 0, beta = 1/32 in the paper).
+ * Output x_j stands for u_j = ((x_j * 2^r) mod 2^32) / 2^32 (its r leading
+ * bits dropped); u_j visits [0, 2^-b) when the b bits after the r dropped
+ * ones are all zero.  A gap is the number of consecutive non-visits before a
+ * visit, counted from the start of the sequence; a trailing run without a
+ * visit is not a gap.  hist[s] (s < t) counts the gaps of length s and
+ * hist[t] those of length >= t (t + 1 entries, overwritten).
+ * Requires b >= 1, r + b <= 32, t >= 1.  Returns 0, or -1 on bad arguments. */
+int omtgp_gap_histogram(const uint32_t* x, uint64_t n, unsigned r, unsigned b, unsigned t,
+                        uint64_t* hist);
+
+/* Test 100 (Hamming-weight independence; r = 25, s = 5, L = 1200 in the
+ * paper).  The s bits after the r dropped leading bits of each output, most
+ * significant first, are concatenated into one bit string, cut into blocks
+ * of L bits (L a multiple of s) with Hamming weights W_0, W_1, ...  Each
+ * pair of successive non-overlapping blocks (W_2i, W_2i+1) is counted in
+ * table[c(W_2i) * C + c(W_2i+1)], where c(w) is the number of class bounds
+ * <= w (bounds ascending; C = n_bounds + 1 classes).  Blocks of an
+ * incomplete trailing pair are ignored.  table has C * C entries
+ * (overwritten).  Requires 1 <= s, r + s <= 32, L % s == 0, L > 0.
+ * Returns 0, or -1 on bad arguments. */
+int omtgp_hamming_pairs(const uint32_t* x, uint64_t n, unsigned r, unsigned s, unsigned L,
+                        const uint32_t* bounds, unsigned n_bounds, uint64_t* table);
 
 #ifdef __cplusplus
 }

@@ -41,10 +41,28 @@ MUTANTS = {
                    "p->mask = 0xFFFFFFFFu << (uint32_t)(r - 1);"),
 }
 
+# Mistakes in the statistics of tests 35 / 100, caught by their own pins.
+QUALITY_MUTANTS = {
+    "gap_off_by_one": ("hist[run < t ? run : t] += 1;", "hist[run + 1 < t ? run + 1 : t] += 1;"),
+    "gap_run_not_reset": ("            run = 0;\n        } else {",
+                          "            run = 1;\n        } else {"),
+    "gap_field_position": ("uint64_t v = ((uint64_t)x << r) & 0xFFFFFFFFull;   /* drop r leading bits */",
+                           "uint64_t v = ((uint64_t)x << (r + 1)) & 0xFFFFFFFFull;"),
+    "hamming_class_strict": ("if (bounds[i] <= w)", "if (bounds[i] < w)"),
+    "hamming_pair_transposed": ("table[cls[0] * C + cls[1]] += 1;", "table[cls[1] * C + cls[0]] += 1;"),
+    "hamming_field_width": ("uint32_t field = (uint32_t)(v >> (32 - s));",
+                            "uint32_t field = (uint32_t)(v >> (31 - s));"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(QUALITY_MUTANTS))
 def test_pins_reject_planted_mistake(name, tmp_path):
-    before, after = MUTANTS[name]
+    if name in MUTANTS:
+        before, after = MUTANTS[name]
+        pins = "test_oracle_pins.py"
+    else:
+        before, after = (x.replace("\\n", "\n") for x in QUALITY_MUTANTS[name])
+        pins = "test_quality_oracle.py"
     src = open(SRC).read()
     assert src.count(before) == 1, name
     mutant_c = tmp_path / "mutant.c"
@@ -56,6 +74,6 @@ def test_pins_reject_planted_mistake(name, tmp_path):
                            "-lpthread"])
     env = dict(os.environ, MTGP_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "pins accepted mutant %s:\n%s" % (name, r.stdout[-2000:])
