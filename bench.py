@@ -340,6 +340,25 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         e2e = measure_e2e(mtgp, torch, st, ids, counts, stream, args)
 
+    # quality statistics of this launch's output (tests 35 and 100, Sec. 4.2)
+    qual = None
+    if rank == 0 and args.quality:
+        from paper_1501_07701_gb300 import quality
+        bounds = quality.default_hamming_bounds(1200, 4)
+        q0, q1, q2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        q0.record(stream)
+        hist = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128, stream=stream)
+        q1.record(stream)
+        tab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds, stream=stream)
+        q2.record(stream)
+        stream.synchronize()
+        g = quality.gap_test(hist.sum(axis=0), b=5)
+        hm = quality.hamming_test(tab.sum(axis=0), L=1200, bounds=bounds)
+        qual = {"gap_test": {"r": 25, "beta": "1/32", "t": 128, "gnum_s": total / (q0.elapsed_time(q1) * 1e6),
+                             "pooled": g},
+                "hamming_indep": {"r": 25, "s": 5, "L": 1200, "classes": len(bounds) + 1,
+                                  "gnum_s": total / (q1.elapsed_time(q2) * 1e6), "pooled": hm}}
+
     serving = None
     if rank == 0 and args.serving_seconds > 0:
         del plan
@@ -379,6 +398,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": args.steps * info["kernel_launches"],
             "bit_exact_sample": bit_exact,
             "serving": serving,
+            "quality": qual,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -465,6 +485,8 @@ def main():
                          "(skips autotuning)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quality", action="store_true",
+                    help="also run the gap and Hamming-weight statistics over the generated output")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

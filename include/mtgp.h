@@ -368,6 +368,38 @@ mtgp_status mtgp_server_run_trace(mtgp_server_t server, const double* t_arrival,
 mtgp_status mtgp_server_free(mtgp_server_t server);
 
 /* ---------------------------------------------------------------------- */
+/* Quality statistics: the data reductions of the paper's two failing     */
+/* BigCrush tests (Sec. 4.2), over outputs already in device memory       */
+/* ---------------------------------------------------------------------- */
+
+/* Test 35 (gap test; the paper runs r = 25, alpha = 0, beta = 1/32, i.e.
+ * b = 5).  `values` is a device pointer to n_seq sequences of 32-bit outputs
+ * laid out back to back, sequence i holding counts[i] values (host array).
+ * A value visits [0, 2^-b) when the b bits after its r dropped leading bits
+ * are zero; a gap is the run of non-visits before a visit, counted from the
+ * start of its sequence (a trailing run without a visit is not a gap).
+ * hist (host, n_seq x (t+1), overwritten): hist[i*(t+1) + k] = number of
+ * gaps of length k in sequence i for k < t, and of length >= t for k = t.
+ * Requires b >= 1, r + b <= 32, 1 <= t <= 1023.  Runs on cuda_stream and
+ * returns when hist is filled; allocates and frees its own device scratch. */
+mtgp_status mtgp_gap_histogram(const uint32_t* values, const uint64_t* counts, uint32_t n_seq,
+                               uint32_t r, uint32_t b, uint32_t t, uint64_t* hist,
+                               void* cuda_stream);
+
+/* Test 100 (Hamming-weight independence; the paper runs r = 25, s = 5,
+ * L = 1200).  The s bits after the r dropped leading bits of each value form
+ * a bit string cut into L-bit blocks (L a multiple of s) per sequence; each
+ * pair of successive non-overlapping blocks is counted in
+ * table[i*C*C + c(W1)*C + c(W2)] (host, n_seq x C x C, overwritten), where
+ * W1, W2 are the pair's Hamming weights and c(w) = number of bounds <= w
+ * (bounds: host array of n_bounds ascending values, C = n_bounds + 1 <= 16).
+ * Blocks of an incomplete trailing pair are ignored.  Same layout, stream
+ * and scratch conventions as mtgp_gap_histogram. */
+mtgp_status mtgp_hamming_pairs(const uint32_t* values, const uint64_t* counts, uint32_t n_seq,
+                               uint32_t r, uint32_t s, uint32_t L, const uint32_t* bounds,
+                               uint32_t n_bounds, uint64_t* table, void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
 
 /* Message for the last failure on the calling thread ("" if none). */
 const char* mtgp_last_error(void);

@@ -1,0 +1,385 @@
+// Data reductions behind the paper's two failing BigCrush tests (Sec. 4.2),
+// run on the GPU over sequences of 32-bit outputs that are already in device
+// memory (for instance the output of mtgp_generate_u32):
+//
+//   test 35, the gap test: a value visits [0, 2^-b) when the b bits after its
+//   r dropped leading bits are zero; a gap is the run of non-visits before a
+//   visit, counted from the start of its sequence; the reduction is the
+//   histogram of gap lengths (lengths >= t pooled).
+//
+//   test 100, Hamming-weight independence: the s bits after the r dropped
+//   leading bits of each value form a bit string cut into L-bit blocks; each
+//   pair of successive blocks is counted in a table of (weight class of the
+//   first, weight class of the second).
+//
+// Both read every value once and are bound by HBM read bandwidth.  The
+// chi-square statistics are computed on the host from the counts.
+#include <algorithm>
+#include <vector>
+
+#include "mtgp_runtime.h"
+
+using namespace mtgp;
+
+namespace {
+
+constexpr uint32_t kChunk = 1u << 16;       // values per gap-test work unit (one warp)
+constexpr uint32_t kMaxT = 1023;            // largest pooled gap class
+constexpr uint32_t kMaxClasses = 16;        // largest number of weight classes
+constexpr int kWarps = 8;                   // warps per CTA of both kernels
+
+struct GapChunk {
+    uint64_t start;   // first value (element offset into `values`)
+    uint32_t len;     // values in the chunk (<= kChunk)
+    uint32_t seq;     // sequence it belongs to
+};
+
+// Per chunk: the run of non-visits before its first visit (the whole length
+// if it has none), the run after its last visit, and whether it has a visit.
+// Gaps that cross chunk boundaries are completed on the host from these.
+struct GapEdge {
+    uint32_t prefix;
+    uint32_t suffix;
+    uint32_t has_visit;
+    uint32_t pad;
+};
+
+__device__ __forceinline__ bool field_is_zero(uint32_t x, uint32_t r, uint32_t width)
+{
+    // the `width` bits after the r dropped leading bits (r + width <= 32, width >= 1)
+    return ((x << r) >> (32u - width)) == 0u;
+}
+
+// One warp per chunk.  Per group of 32 consecutive values the visits form a
+// ballot mask B; a visiting lane's gap is the distance to the nearest lower
+// visiting lane, or the carried run D plus its lane index if it is the
+// group's first visit.  The ballot and every shuffle run in warp-uniform
+// control flow; the per-lane branch holds only shared-memory atomics.
+__global__ void __launch_bounds__(kWarps * 32) mtgp_gap_kernel(const uint32_t* __restrict__ values,
+                                                              const GapChunk* __restrict__ chunks,
+                                                              uint32_t n_chunks, uint32_t r, uint32_t b,
+                                                              uint32_t t,
+                                                              unsigned long long* __restrict__ hist,
+                                                              GapEdge* __restrict__ edges)
+{
+    __shared__ uint32_t h_all[kWarps][kMaxT + 1];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t* h = h_all[warp];
+    const uint32_t gwarp = blockIdx.x * kWarps + warp, nwarps = gridDim.x * kWarps;
+    for (uint32_t c = gwarp; c < n_chunks; c += nwarps) {
+        const GapChunk ch = chunks[c];
+        for (uint32_t i = lane; i <= t; i += 32u)
+            h[i] = 0u;
+        __syncwarp();
+        const uint32_t* v = values + ch.start;
+        uint32_t D = 0, P = 0;
+        bool seen = false;
+        // 8 groups of 32 values per round: their loads are all in flight
+        // before the first group is scanned
+        constexpr uint32_t kG = 8;
+        for (uint32_t base0 = 0; base0 < ch.len; base0 += 32u * kG) {
+            uint32_t xs[kG];
+#pragma unroll
+            for (uint32_t g = 0; g < kG; ++g) {
+                const uint32_t idx = base0 + 32u * g + lane;
+                xs[g] = idx < ch.len ? __ldcs(v + idx) : 0u;
+            }
+#pragma unroll
+            for (uint32_t g = 0; g < kG; ++g) {
+                const uint32_t base = base0 + 32u * g;
+                if (base >= ch.len)
+                    break;
+                const bool in = base + lane < ch.len && field_is_zero(xs[g], r, b);
+                const uint32_t B = __ballot_sync(0xFFFFFFFFu, in);
+                if (in) {
+                    const uint32_t below = B & ((1u << lane) - 1u);
+                    if (below) {
+                        const uint32_t gap = lane - (31u - __clz(below)) - 1u;
+                        atomicAdd(&h[min(gap, t)], 1u);
+                    } else if (seen) {
+                        atomicAdd(&h[min(D + lane, t)], 1u);
+                    }
+                }
+                const uint32_t nv = min(32u, ch.len - base);
+                if (B) {
+                    if (!seen)
+                        P = D + (uint32_t)(__ffs(B) - 1);
+                    seen = true;
+                    D = nv - 1u - (31u - __clz(B));
+                } else {
+                    D += nv;
+                }
+            }
+        }
+        __syncwarp();
+        unsigned long long* hs = hist + (size_t)ch.seq * (t + 1u);
+        for (uint32_t i = lane; i <= t; i += 32u)
+            if (h[i])
+                atomicAdd(hs + i, (unsigned long long)h[i]);
+        if (lane == 0) {
+            GapEdge e;
+            e.prefix = seen ? P : ch.len;
+            e.suffix = D;
+            e.has_visit = seen ? 1u : 0u;
+            e.pad = 0;
+            edges[c] = e;
+        }
+        __syncwarp();
+    }
+}
+
+// One warp per pair of blocks (2K values, K = L / s).  Each lane sums the
+// field weights of its values of each block; two warp reductions give the
+// block weights; lane 0 classifies them and counts the pair in the warp's
+// table, which is flushed whenever the warp moves to another sequence.
+__global__ void __launch_bounds__(kWarps * 32) mtgp_hamming_kernel(const uint32_t* __restrict__ values,
+                                                                  const uint64_t* __restrict__ seq_start,
+                                                                  const uint64_t* __restrict__ pair_base,
+                                                                  uint32_t n_seq, uint64_t n_pairs,
+                                                                  uint32_t r, uint32_t s, uint32_t K,
+                                                                  const uint32_t* __restrict__ bounds,
+                                                                  uint32_t n_bounds,
+                                                                  unsigned long long* __restrict__ table)
+{
+    __shared__ uint32_t tab_all[kWarps][kMaxClasses * kMaxClasses];
+    __shared__ uint32_t bnd[kMaxClasses];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (threadIdx.x < n_bounds)
+        bnd[threadIdx.x] = bounds[threadIdx.x];
+    const uint32_t C = n_bounds + 1u;
+    uint32_t* tab = tab_all[warp];
+    for (uint32_t i = lane; i < C * C; i += 32u)
+        tab[i] = 0u;
+    __syncthreads();
+    // contiguous ranges of pairs per warp, so the sequence changes rarely
+    const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
+    const uint64_t gwarp = (uint64_t)blockIdx.x * kWarps + warp;
+    const uint64_t per = (n_pairs + nwarps - 1) / nwarps;
+    const uint64_t p0 = gwarp * per, p1 = min(p0 + per, n_pairs);
+    uint32_t seq = 0xFFFFFFFFu;
+    uint64_t seq_end = 0;
+    bool dirty = false;
+    for (uint64_t p = p0; p < p1; ++p) {
+        if (seq == 0xFFFFFFFFu || p >= seq_end) {
+            if (dirty) {
+                __syncwarp();
+                for (uint32_t i = lane; i < C * C; i += 32u) {
+                    if (tab[i])
+                        atomicAdd(table + (size_t)seq * C * C + i, (unsigned long long)tab[i]);
+                    tab[i] = 0u;
+                }
+                __syncwarp();
+                dirty = false;
+            }
+            // the sequence holding pair p: last s with pair_base[s] <= p
+            uint32_t lo = 0, hi = n_seq;
+            while (hi - lo > 1u) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (pair_base[mid] <= p)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            seq = lo;
+            seq_end = pair_base[lo + 1];
+        }
+        const uint32_t* v = values + seq_start[seq] + (p - pair_base[seq]) * 2ull * K;
+        uint32_t wa = 0, wb = 0;
+#pragma unroll 4
+        for (uint32_t j = lane; j < 2u * K; j += 32u) {
+            const uint32_t x = __ldcs(v + j);
+            const uint32_t w = __popc((x << r) >> (32u - s));
+            if (j < K)
+                wa += w;
+            else
+                wb += w;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wa += __shfl_xor_sync(0xFFFFFFFFu, wa, o);
+            wb += __shfl_xor_sync(0xFFFFFFFFu, wb, o);
+        }
+        if (lane == 0) {
+            uint32_t ca = 0, cb = 0;
+            for (uint32_t i = 0; i < n_bounds; ++i) {
+                ca += bnd[i] <= wa;
+                cb += bnd[i] <= wb;
+            }
+            tab[ca * C + cb] += 1u;
+        }
+        dirty = true;
+    }
+    __syncwarp();
+    if (dirty)
+        for (uint32_t i = lane; i < C * C; i += 32u)
+            if (tab[i])
+                atomicAdd(table + (size_t)seq * C * C + i, (unsigned long long)tab[i]);
+}
+
+int grid_for(const void* fn)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kWarps * 32, 0);
+    return std::max(1, sms * std::max(per, 1));
+}
+
+// Device scratch of one call, released on every exit path.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    cudaError_t alloc(void** p, size_t bytes)
+    {
+        cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), s);
+        if (e == cudaSuccess)
+            ptrs.push_back(*p);
+        return e;
+    }
+    ~Scratch()
+    {
+        for (void* p : ptrs)
+            cudaFreeAsync(p, s);
+    }
+};
+
+#define Q_TRY(call, what)                 \
+    do {                                  \
+        cudaError_t e_ = (call);          \
+        if (e_ != cudaSuccess)            \
+            return fail_cuda(e_, what);   \
+    } while (0)
+
+}  // namespace
+
+extern "C" mtgp_status mtgp_gap_histogram(const uint32_t* values, const uint64_t* counts, uint32_t n_seq,
+                                          uint32_t r, uint32_t b, uint32_t t, uint64_t* hist,
+                                          void* cuda_stream)
+{
+    try {
+        if (!counts || !hist || n_seq == 0)
+            return fail(MTGP_EINVAL, "null argument or no sequence");
+        if (b < 1 || r + b > 32 || t < 1 || t > kMaxT)
+            return fail(MTGP_EINVAL, "need b >= 1, r + b <= 32, 1 <= t <= %u", kMaxT);
+        uint64_t total = 0;
+        std::vector<GapChunk> chunks;
+        std::vector<uint64_t> seq_first_chunk(n_seq + 1);
+        for (uint32_t i = 0; i < n_seq; ++i) {
+            seq_first_chunk[i] = chunks.size();
+            for (uint64_t o = 0; o < counts[i]; o += kChunk) {
+                GapChunk c;
+                c.start = total + o;
+                c.len = (uint32_t)std::min<uint64_t>(kChunk, counts[i] - o);
+                c.seq = i;
+                chunks.push_back(c);
+            }
+            total += counts[i];
+        }
+        seq_first_chunk[n_seq] = chunks.size();
+        std::fill(hist, hist + (size_t)n_seq * (t + 1), 0ull);
+        if (total && !values)
+            return fail(MTGP_EINVAL, "null values pointer");
+        if (chunks.empty())
+            return ok();
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        std::vector<GapEdge> edges(chunks.size());
+        {
+            Scratch sc(s);
+            void *d_chunks, *d_hist, *d_edges;
+            const size_t hbytes = (size_t)n_seq * (t + 1) * sizeof(unsigned long long);
+            Q_TRY(sc.alloc(&d_chunks, chunks.size() * sizeof(GapChunk)), "cudaMallocAsync");
+            Q_TRY(sc.alloc(&d_hist, hbytes), "cudaMallocAsync");
+            Q_TRY(sc.alloc(&d_edges, chunks.size() * sizeof(GapEdge)), "cudaMallocAsync");
+            Q_TRY(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(GapChunk),
+                                  cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+            Q_TRY(cudaMemsetAsync(d_hist, 0, hbytes, s), "cudaMemsetAsync");
+            const int grid = std::min<long long>(grid_for((const void*)mtgp_gap_kernel),
+                                                 ((long long)chunks.size() + kWarps - 1) / kWarps);
+            mtgp_gap_kernel<<<grid, kWarps * 32, 0, s>>>(values, (const GapChunk*)d_chunks,
+                                                          (uint32_t)chunks.size(), r, b, t,
+                                                          (unsigned long long*)d_hist, (GapEdge*)d_edges);
+            Q_TRY(cudaGetLastError(), "gap kernel launch");
+            Q_TRY(cudaMemcpyAsync(hist, d_hist, hbytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+            Q_TRY(cudaMemcpyAsync(edges.data(), d_edges, edges.size() * sizeof(GapEdge),
+                                  cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+            Q_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        }
+        // gaps that cross chunk boundaries (and each sequence's first gap)
+        for (uint32_t i = 0; i < n_seq; ++i) {
+            uint64_t run = 0;
+            for (uint64_t c = seq_first_chunk[i]; c < seq_first_chunk[i + 1]; ++c) {
+                if (edges[c].has_visit) {
+                    const uint64_t gap = run + edges[c].prefix;
+                    hist[(size_t)i * (t + 1) + std::min<uint64_t>(gap, t)] += 1;
+                    run = edges[c].suffix;
+                } else {
+                    run += chunks[c].len;
+                }
+            }
+        }
+        return ok();
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+extern "C" mtgp_status mtgp_hamming_pairs(const uint32_t* values, const uint64_t* counts, uint32_t n_seq,
+                                          uint32_t r, uint32_t s, uint32_t L, const uint32_t* bounds,
+                                          uint32_t n_bounds, uint64_t* table, void* cuda_stream)
+{
+    try {
+        if (!counts || !table || n_seq == 0 || (n_bounds && !bounds))
+            return fail(MTGP_EINVAL, "null argument or no sequence");
+        if (s < 1 || r + s > 32 || L == 0 || L % s != 0 || L / s > (1u << 24))
+            return fail(MTGP_EINVAL, "need s >= 1, r + s <= 32, L > 0 a multiple of s");
+        if (n_bounds + 1 > kMaxClasses)
+            return fail(MTGP_EINVAL, "at most %u weight classes", kMaxClasses);
+        for (uint32_t i = 1; i < n_bounds; ++i)
+            if (bounds[i] < bounds[i - 1])
+                return fail(MTGP_EINVAL, "class bounds must be ascending");
+        const uint32_t K = L / s, C = n_bounds + 1;
+        std::vector<uint64_t> seq_start(n_seq), pair_base(n_seq + 1);
+        uint64_t total = 0, pairs = 0;
+        for (uint32_t i = 0; i < n_seq; ++i) {
+            seq_start[i] = total;
+            pair_base[i] = pairs;
+            pairs += counts[i] / (2ull * K);
+            total += counts[i];
+        }
+        pair_base[n_seq] = pairs;
+        std::fill(table, table + (size_t)n_seq * C * C, 0ull);
+        if (total && !values)
+            return fail(MTGP_EINVAL, "null values pointer");
+        if (pairs == 0)
+            return ok();
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        Scratch sc(st);
+        void *d_start, *d_base, *d_bounds, *d_table;
+        const size_t tbytes = (size_t)n_seq * C * C * sizeof(unsigned long long);
+        Q_TRY(sc.alloc(&d_start, n_seq * sizeof(uint64_t)), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_base, (n_seq + 1) * sizeof(uint64_t)), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_bounds, (n_bounds + 1) * sizeof(uint32_t)), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_table, tbytes), "cudaMallocAsync");
+        Q_TRY(cudaMemcpyAsync(d_start, seq_start.data(), n_seq * sizeof(uint64_t), cudaMemcpyHostToDevice, st),
+              "cudaMemcpyAsync");
+        Q_TRY(cudaMemcpyAsync(d_base, pair_base.data(), (n_seq + 1) * sizeof(uint64_t),
+                              cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+        if (n_bounds)
+            Q_TRY(cudaMemcpyAsync(d_bounds, bounds, n_bounds * sizeof(uint32_t), cudaMemcpyHostToDevice, st),
+                  "cudaMemcpyAsync");
+        Q_TRY(cudaMemsetAsync(d_table, 0, tbytes, st), "cudaMemsetAsync");
+        const int grid = (int)std::min<uint64_t>((uint64_t)grid_for((const void*)mtgp_hamming_kernel),
+                                                 (pairs + kWarps - 1) / kWarps);
+        mtgp_hamming_kernel<<<grid, kWarps * 32, 0, st>>>(values, (const uint64_t*)d_start,
+                                                           (const uint64_t*)d_base, n_seq, pairs, r, s, K,
+                                                           (const uint32_t*)d_bounds, n_bounds,
+                                                           (unsigned long long*)d_table);
+        Q_TRY(cudaGetLastError(), "Hamming kernel launch");
+        Q_TRY(cudaMemcpyAsync(table, d_table, tbytes, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+        Q_TRY(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        return ok();
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}

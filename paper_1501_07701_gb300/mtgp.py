@@ -83,6 +83,10 @@ _SIGS = {
     "mtgp_params_get": [_VP, ctypes.POINTER(ParamsDesc)],
     "mtgp_params_free": [_VP],
     "mtgp_init_statuses": [_VP, _U32P, ctypes.c_uint32, _VP, ctypes.POINTER(_VP)],
+    "mtgp_gap_histogram": [_VP, _U64P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                           _U64P, _VP],
+    "mtgp_hamming_pairs": [_VP, _U64P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                           _U32P, ctypes.c_uint32, _U64P, _VP],
     "mtgp_init_statuses_multi": [ctypes.POINTER(_VP), ctypes.c_uint32, _U32P, _U32P, ctypes.c_uint32,
                                  _VP, ctypes.POINTER(_VP)],
     "mtgp_set_statuses": [_VP, _U32P, _VP],
@@ -506,3 +510,27 @@ def mtgp_server_run_trace(server: Server, t_arrival, ids, counts, fmts, mode=0, 
           _p64(offs) if record else None, ctypes.byref(st))
     return lat, offs, {"requests": st.requests, "numbers": st.numbers, "ticks": st.ticks,
                        "elapsed": st.elapsed, "busy_wait": st.busy_wait}
+
+
+# ---------------------------------------------------------------------------
+# Quality statistics (Sec. 4.2, tests 35 and 100) over device sequences
+# ---------------------------------------------------------------------------
+def mtgp_gap_histogram(values, counts, r=25, b=5, t=128, stream=None) -> np.ndarray:
+    """Gap-length histograms of the device sequences in `values` (back to
+    back, lengths `counts`): array (n_seq, t + 1)."""
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    hist = np.zeros((counts.size, t + 1), dtype=np.uint64)
+    _call("mtgp_gap_histogram", _dev_ptr(values, int(counts.sum())), _p64(counts), counts.size, r, b, t,
+          _p64(hist), _stream_handle(stream))
+    return hist
+
+
+def mtgp_hamming_pairs(values, counts, r=25, s=5, L=1200, bounds=(), stream=None) -> np.ndarray:
+    """Tables of successive block-weight classes: array (n_seq, C, C)."""
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    bnd = np.ascontiguousarray(bounds, dtype=np.uint32)
+    C = bnd.size + 1
+    table = np.zeros((counts.size, C, C), dtype=np.uint64)
+    _call("mtgp_hamming_pairs", _dev_ptr(values, int(counts.sum())), _p64(counts), counts.size, r, s, L,
+          _p32(bnd) if bnd.size else None, bnd.size, _p64(table), _stream_handle(stream))
+    return table
