@@ -368,6 +368,33 @@ mtgp_status mtgp_server_run_trace(mtgp_server_t server, const double* t_arrival,
 mtgp_status mtgp_server_free(mtgp_server_t server);
 
 /* ---------------------------------------------------------------------- */
+/* Jump-ahead (sub-streams of one generator, Sec. 2)                      */
+/* ---------------------------------------------------------------------- */
+
+/* Advances stream ids[i] by jumps[i] numbers, exactly as generating and
+ * discarding them would, in time independent of the jump length: the state
+ * after J steps is one step applied to g(F) w, g = t^(J-1) mod mu, where mu
+ * annihilates the transition (see mtgp_params_minpoly).  Jumps of one stream
+ * add up.  ids and jumps are host arrays of n entries.  The first jump for a
+ * parameter set computes mu on the host (Berlekamp-Massey, about a second
+ * for Mexp 44497); each distinct jump length costs a polynomial power on the
+ * host (cached).  Runs on cuda_stream and returns when the states are
+ * updated.  MTGP_EINVAL for an id out of range or a 64-bit overflow. */
+mtgp_status mtgp_jump(mtgp_streams_t streams, const uint32_t* ids, const uint64_t* jumps, uint32_t n,
+                      void* cuda_stream);
+
+/* The polynomial mu over GF(2) that the jump uses for this parameter set:
+ * the least common multiple of minimal polynomials of output bit sequences,
+ * checked to annihilate the transition on random states (mu(F) w has only
+ * the masked bits of its oldest word set).  deg mu <= Mexp; equality with
+ * mu irreducible means the period 2^Mexp - 1 of a Mersenne-prime Mexp.
+ * words (host, may be null to query the degree) receives the coefficients,
+ * bit i of the little-endian 64-bit words = coefficient of t^i; cap_words
+ * must be >= degree/64 + 1.  Pure host computation, cached. */
+mtgp_status mtgp_params_minpoly(mtgp_params_t params, uint64_t* words, uint32_t cap_words,
+                                int32_t* degree);
+
+/* ---------------------------------------------------------------------- */
 /* Quality statistics: the data reductions of the paper's two failing     */
 /* BigCrush tests (Sec. 4.2), over outputs already in device memory       */
 /* ---------------------------------------------------------------------- */

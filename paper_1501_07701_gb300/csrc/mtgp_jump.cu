@@ -1,0 +1,590 @@
+// Jump-ahead: advance streams by J numbers without producing them.
+//
+// The paper motivates splitting one generator into sub-streams (Sec. 2); for
+// an F2-linear generator the exact way is a polynomial jump.  The state of a
+// stream is the window w = (x_c .. x_{c+N-1}); one step F maps it to
+// (x_{c+1} .. x_{c+N}).  F is linear over GF(2).  Its kernel K holds the
+// windows that are zero except in the r = 32N - Mexp low bits of the oldest
+// word (the recursion masks those bits away), and F(K) = 0.  Let mu be a
+// polynomial with mu(F) w in K for every w (the minimal polynomial of the
+// transition on the quotient by K, degree <= Mexp).  Then F mu(F) = 0, and
+// writing t^(J-1) = q mu + g gives
+//
+//     F^J = q(F) mu(F) F + g(F) F = F g(F),
+//
+// so the state after J steps is one ordinary step applied to
+// g(F) w = XOR over the set bits k of g of the window (x_k .. x_{k+N-1}) of
+// the sequence that starts at w.
+//
+// Host side: mu comes from Berlekamp-Massey on bit sequences of the
+// recursion (run on the host), combined by LCM until it annihilates random
+// states; g = t^(J-1) mod mu by square-and-multiply.  Both are cached per
+// parameter set.  Device side: one CTA per stream expands the sequence
+// x_0 .. x_{D+N-2} (D = deg g + 1) in shared memory, every warp XORs the
+// windows of its share of g's set bits into the N-word accumulator, and the
+// last step is applied to the result.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <random>
+#include <vector>
+
+#include "mtgp_runtime.h"
+
+using namespace mtgp;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Polynomials over GF(2) as bit vectors (bit i = coefficient of t^i)
+// ---------------------------------------------------------------------------
+using Poly = std::vector<uint64_t>;
+
+int degree(const Poly& a)
+{
+    for (size_t w = a.size(); w-- > 0;)
+        if (a[w])
+            return (int)(w * 64 + 63 - __builtin_clzll(a[w]));
+    return -1;
+}
+
+void trim(Poly& a)
+{
+    while (!a.empty() && a.back() == 0)
+        a.pop_back();
+}
+
+bool bit(const Poly& a, size_t i) { return i / 64 < a.size() && ((a[i / 64] >> (i % 64)) & 1u); }
+
+// a ^= b << sh
+void xor_shifted(Poly& a, const Poly& b, size_t sh)
+{
+    const size_t ws = sh / 64, bs = sh % 64;
+    if (a.size() < b.size() + ws + 1)
+        a.resize(b.size() + ws + 1, 0);
+    for (size_t w = 0; w < b.size(); ++w) {
+        if (!b[w])
+            continue;
+        a[w + ws] ^= b[w] << bs;
+        if (bs)
+            a[w + ws + 1] ^= b[w] >> (64 - bs);
+    }
+}
+
+// remainder of a modulo m (deg m >= 0)
+Poly mod(Poly a, const Poly& m)
+{
+    const int dm = degree(m);
+    for (int d = degree(a); d >= dm; d = degree(a))
+        xor_shifted(a, m, (size_t)(d - dm));
+    trim(a);
+    return a;
+}
+
+// quotient and remainder
+void divmod(Poly a, const Poly& m, Poly& q, Poly& r)
+{
+    const int dm = degree(m);
+    q.assign(1, 0);
+    for (int d = degree(a); d >= dm; d = degree(a)) {
+        const size_t sh = (size_t)(d - dm);
+        if (q.size() <= sh / 64)
+            q.resize(sh / 64 + 1, 0);
+        q[sh / 64] ^= 1ull << (sh % 64);
+        xor_shifted(a, m, sh);
+    }
+    trim(a);
+    trim(q);
+    r = a;
+}
+
+Poly mul(const Poly& a, const Poly& b)
+{
+    Poly c;
+    const int db = degree(b);
+    for (int i = 0; i <= db; ++i)
+        if (bit(b, (size_t)i))
+            xor_shifted(c, a, (size_t)i);
+    trim(c);
+    return c;
+}
+
+Poly gcd(Poly a, Poly b)
+{
+    trim(a);
+    trim(b);
+    while (degree(b) >= 0) {
+        Poly r = mod(a, b);
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
+// a^2 mod m: squaring spreads the bits (no cross terms over GF(2))
+Poly sqr_mod(const Poly& a, const Poly& m)
+{
+    Poly s(a.size() * 2 + 1, 0);
+    for (size_t w = 0; w < a.size(); ++w)
+        for (int i = 0; i < 64; ++i)
+            if ((a[w] >> i) & 1u) {
+                const size_t j = 2 * (w * 64 + (size_t)i);
+                s[j / 64] |= 1ull << (j % 64);
+            }
+    return mod(s, m);
+}
+
+// t^e mod m (left-to-right square-and-multiply; multiplying by t is a shift)
+Poly pow_t_mod(uint64_t e, const Poly& m)
+{
+    Poly r(1, 1ull);   // t^0, reduced: zero only modulo a constant
+    if (degree(m) == 0)
+        r.clear();
+    for (int b = 63; b >= 0; --b) {
+        r = sqr_mod(r, m);
+        if ((e >> b) & 1u) {
+            Poly s;
+            xor_shifted(s, r, 1);
+            r = mod(s, m);
+        }
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// The recursion on the host (words only, no tempering): seq[0..N) = state,
+// then count new words.
+// ---------------------------------------------------------------------------
+struct SetP {
+    uint32_t n, pos, sh1, sh2, mask;
+    uint32_t rec[16];
+};
+
+void host_sequence(const SetP& p, const uint32_t* state, size_t count, std::vector<uint32_t>& seq)
+{
+    seq.assign(state, state + p.n);
+    seq.resize(p.n + count);
+    for (size_t i = 0; i < count; ++i) {
+        uint32_t y = (seq[i] & p.mask) ^ seq[i + 1];
+        y ^= y << p.sh1;
+        y ^= seq[i + p.pos] >> p.sh2;
+        seq[i + p.n] = y ^ p.rec[y & 15u];
+    }
+}
+
+// Berlekamp-Massey over GF(2): the minimal polynomial of the bit sequence
+// s (n bits), as mu(t) = t^L C(1/t) for the connection polynomial C.
+Poly berlekamp_massey(const std::vector<uint8_t>& s)
+{
+    const size_t n = s.size();
+    // reversed sequence, bit-packed: R_k = s_{n-1-k}
+    Poly R((n + 127) / 64, 0);
+    for (size_t k = 0; k < n; ++k)
+        if (s[n - 1 - k])
+            R[k / 64] |= 1ull << (k % 64);
+    auto window = [&](size_t off) -> uint64_t {   // bits R[off .. off+63]
+        const size_t w = off / 64, b = off % 64;
+        uint64_t v = R[w] >> b;
+        if (b && w + 1 < R.size())
+            v |= R[w + 1] << (64 - b);
+        return v;
+    };
+    Poly C(1, 1ull), B(1, 1ull);
+    size_t L = 0;
+    long m = -1;
+    for (size_t i = 0; i < n; ++i) {
+        // discrepancy: sum_{j=0..L} c_j s_{i-j}, s_{i-j} = R_{n-1-i+j}
+        uint64_t acc = 0;
+        const size_t off = n - 1 - i;
+        for (size_t w = 0; w * 64 <= L && w < C.size(); ++w) {
+            uint64_t cw = C[w];
+            if (w * 64 + 64 > L + 1)
+                cw &= (L + 1 - w * 64) >= 64 ? ~0ull : ((1ull << (L + 1 - w * 64)) - 1);
+            acc ^= cw & window(off + w * 64);
+        }
+        if (__builtin_parityll(acc)) {
+            Poly T = C;
+            xor_shifted(C, B, (size_t)((long)i - m));
+            if (2 * L <= i) {
+                L = i + 1 - L;
+                m = (long)i;
+                B = T;
+            }
+        }
+    }
+    Poly mu((L + 64) / 64, 0);
+    for (size_t k = 0; k <= L; ++k)
+        if (bit(C, L - k))
+            mu[k / 64] |= 1ull << (k % 64);
+    trim(mu);
+    return mu;
+}
+
+// True if F mu(F) w = 0 for the sequence of `state`: for j = 1..N the XOR of
+// x_{k+j} over the set bits k of mu is zero.
+bool annihilates(const SetP& p, const Poly& mu, const uint32_t* state)
+{
+    const int d = degree(mu);
+    std::vector<uint32_t> seq;
+    host_sequence(p, state, (size_t)d + p.n + 1, seq);
+    for (uint32_t j = 1; j <= p.n; ++j) {
+        uint32_t acc = 0;
+        for (int k = 0; k <= d; ++k)
+            if (bit(mu, (size_t)k))
+                acc ^= seq[(size_t)k + j];
+        if (acc)
+            return false;
+    }
+    return true;
+}
+
+// mu for a parameter set: LCM of the minimal polynomials of bit sequences
+// (random states, random linear functionals of the words) until it
+// annihilates fresh random states.
+Poly transition_polynomial(const SetP& p, uint32_t mexp)
+{
+    std::mt19937_64 rng(0x9E3779B97F4A7C15ull ^ ((uint64_t)p.pos << 32) ^ p.sh1 ^ ((uint64_t)p.rec[1] << 7));
+    auto random_state = [&](std::vector<uint32_t>& st) {
+        st.resize(p.n);
+        for (auto& v : st)
+            v = (uint32_t)rng();
+    };
+    Poly mu;
+    std::vector<uint32_t> st, seq;
+    for (int round = 0; round < 64; ++round) {
+        random_state(st);
+        const size_t len = 2 * (size_t)mexp + 64;
+        host_sequence(p, st.data(), len, seq);   // N + len words
+        // A random linear functional of the whole state F^i w (every word,
+        // the oldest one masked): states that one step maps to zero can live
+        // in the oldest word or in the low bits of the next one, so a
+        // functional of a single word would not see every part of the
+        // transition.
+        std::vector<uint32_t> f(p.n);
+        for (auto& v : f)
+            v = (uint32_t)rng();
+        f[0] &= p.mask;
+        std::vector<uint8_t> bits(len);
+        for (size_t i = 0; i < len; ++i) {
+            uint32_t acc = 0;
+            for (uint32_t j = 0; j < p.n; ++j)
+                acc ^= seq[i + j] & f[j];
+            bits[i] = (uint8_t)__builtin_parity(acc);
+        }
+        Poly m1 = berlekamp_massey(bits);
+        if (degree(m1) < 0)
+            continue;
+        if (mu.empty()) {
+            mu = m1;
+        } else {
+            Poly q, r;
+            divmod(mu, gcd(mu, m1), q, r);
+            mu = mul(q, m1);
+        }
+        if (degree(mu) > (int)mexp)
+            break;   // cannot happen for a linear recursion of this state size
+        // A polynomial that does not annihilate the transition still passes
+        // the check on a random state with probability at most 1/2 (the
+        // states it fails on are the complement of a proper subspace), so 20
+        // passing states leave a false acceptance below 1e-6.
+        bool all = true;
+        for (int t = 0; t < 20 && all; ++t) {
+            random_state(st);
+            all = annihilates(p, mu, st.data());
+        }
+        if (all)
+            return mu;
+    }
+    return Poly();
+}
+
+SetP set_of(const KParams& k, const KSet* ks)
+{
+    SetP p;
+    p.n = k.n;
+    p.mask = k.mask;
+    p.pos = ks ? ks->pos : k.pos;
+    p.sh1 = ks ? ks->sh1 : k.sh1;
+    p.sh2 = ks ? ks->sh2 : k.sh2;
+    for (int i = 0; i < 16; ++i)
+        p.rec[i] = ks ? ks->rec[i] : k.rec[i];
+    return p;
+}
+
+// Caches keyed by the parameter set's fields (and the jump length).
+std::mutex g_cache_mutex;
+std::map<std::vector<uint32_t>, Poly> g_mu_cache;
+std::map<std::pair<std::vector<uint32_t>, uint64_t>, Poly> g_jump_cache;
+
+std::vector<uint32_t> key_of(const SetP& p)
+{
+    std::vector<uint32_t> k = {p.n, p.pos, p.sh1, p.sh2, p.mask};
+    k.insert(k.end(), p.rec, p.rec + 16);
+    return k;
+}
+
+const Poly* cached_mu(const SetP& p, uint32_t mexp)
+{
+    const auto key = key_of(p);
+    {
+        std::lock_guard<std::mutex> g(g_cache_mutex);
+        auto it = g_mu_cache.find(key);
+        if (it != g_mu_cache.end())
+            return it->second.empty() ? nullptr : &it->second;
+    }
+    Poly mu = transition_polynomial(p, mexp);
+    std::lock_guard<std::mutex> g(g_cache_mutex);
+    auto& slot = g_mu_cache.emplace(key, std::move(mu)).first->second;   // first writer wins
+    return slot.empty() ? nullptr : &slot;
+}
+
+// ---------------------------------------------------------------------------
+// Device: one CTA per (stream, jump).  Shared memory: the sequence S[0 .. D+N-1)
+// and the N-word accumulator.  Every wait is a __syncthreads on uniform
+// control flow; no spin waits.
+// ---------------------------------------------------------------------------
+struct JumpItem {
+    uint32_t stream;
+    uint32_t poly;       // index of g among the launch's polynomials
+    uint32_t deg;        // deg g (g != 0)
+    uint32_t set;        // parameter-set index (per-stream sets) or 0
+};
+
+__global__ void __launch_bounds__(256) mtgp_jump_kernel(const KParams P, uint32_t* __restrict__ states,
+                                                       const JumpItem* __restrict__ items,
+                                                       const uint32_t* __restrict__ polys,
+                                                       uint32_t poly_words,
+                                                       const KSet* __restrict__ sets)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    const JumpItem it = items[blockIdx.x];
+    const uint32_t N = P.n, D = it.deg + 1u;
+    uint32_t pos = P.pos, sh1 = P.sh1, sh2 = P.sh2;
+    const uint32_t* rec = P.rec;
+    if (sets) {
+        const KSet& ks = sets[it.set];
+        pos = ks.pos;
+        sh1 = ks.sh1;
+        sh2 = ks.sh2;
+        rec = ks.rec;
+    }
+    uint32_t* S = sm;                 // D + N - 1 words
+    uint32_t* acc = sm + D + N - 1u;  // N words
+    __shared__ uint32_t R[16];
+    if (threadIdx.x < 16)
+        R[threadIdx.x] = rec[threadIdx.x];
+    uint32_t* g = states + (size_t)it.stream * P.np;
+    for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) {
+        S[j] = g[j];
+        acc[j] = 0u;
+    }
+    __syncthreads();
+    // expand: S[i + N] for i = 0 .. D-2, Wc words per step (each reads only
+    // words produced before the step: Wc <= N - pos)
+    const uint32_t Wc = min(32u, N - pos);
+    for (uint32_t i0 = 0; i0 + 1u < D; i0 += Wc) {
+        const uint32_t i = i0 + threadIdx.x;
+        uint32_t v = 0;
+        const bool act = threadIdx.x < Wc && i + 1u < D;
+        if (act) {
+            uint32_t y = (S[i] & P.mask) ^ S[i + 1u];
+            y ^= y << sh1;
+            y ^= S[i + pos] >> sh2;
+            v = y ^ R[y & 15u];
+        }
+        __syncthreads();
+        if (act)
+            S[i + N] = v;
+        __syncthreads();
+    }
+    // accumulate: warp w takes the set bits k of g with k / 32 = w (mod warps)
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t* gp = polys + (size_t)it.poly * poly_words;
+    for (uint32_t j0 = 0; j0 < N; j0 += 32u * 8u) {
+        uint32_t a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t w = warp; w * 32u < D; w += nw) {
+            uint32_t bits = gp[w];
+            while (bits) {
+                const uint32_t k = w * 32u + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1u;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t j = j0 + 32u * q + lane;
+                    if (j < N)
+                        a[q] ^= S[k + j];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t j = j0 + 32u * q + lane;
+            if (j < N && a[q])
+                atomicXor(&acc[j], a[q]);
+        }
+    }
+    __syncthreads();
+    // one ordinary step on the accumulated window: the state after J steps is
+    // (acc[1] .. acc[N-1], new word), oldest first
+    for (uint32_t j = threadIdx.x; j + 1u < N; j += blockDim.x)
+        g[j] = acc[j + 1u];
+    if (threadIdx.x == 0) {
+        uint32_t y = (acc[0] & P.mask) ^ acc[1];
+        y ^= y << sh1;
+        y ^= acc[pos] >> sh2;
+        g[N - 1u] = y ^ R[y & 15u];
+    }
+}
+
+#define J_TRY(call, what)                 \
+    do {                                  \
+        cudaError_t e_ = (call);          \
+        if (e_ != cudaSuccess)            \
+            return fail_cuda(e_, what);   \
+    } while (0)
+
+}  // namespace
+
+extern "C" mtgp_status mtgp_params_minpoly(mtgp_params_t params, uint64_t* words, uint32_t cap_words,
+                                           int32_t* degree_out)
+{
+    try {
+        if (!params || !degree_out)
+            return fail(MTGP_EINVAL, "null argument");
+        const SetP p = set_of(params->k, nullptr);
+        const Poly* mu = cached_mu(p, params->d.mexp);
+        if (!mu)
+            return fail(MTGP_EINVAL, "no annihilating polynomial found for this parameter set");
+        const int d = degree(*mu);
+        *degree_out = d;
+        const uint32_t need = (uint32_t)(d / 64 + 1);
+        if (words) {
+            if (cap_words < need)
+                return fail(MTGP_EINVAL, "need %u words", need);
+            std::fill(words, words + cap_words, 0ull);
+            std::copy(mu->begin(), mu->end(), words);
+        }
+        return ok();
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+extern "C" mtgp_status mtgp_jump(mtgp_streams_t st, const uint32_t* ids, const uint64_t* jumps, uint32_t n,
+                                 void* cuda_stream)
+{
+    try {
+        if (!st || (n && (!ids || !jumps)))
+            return fail(MTGP_EINVAL, "null argument");
+        DeviceGuard dg(st->device);
+        // total jump per stream (jumps compose additively)
+        std::map<uint32_t, uint64_t> total;
+        for (uint32_t i = 0; i < n; ++i) {
+            if (ids[i] >= st->n_streams)
+                return fail(MTGP_EINVAL, "stream id %u out of range (%u streams)", ids[i], st->n_streams);
+            uint64_t& t = total[ids[i]];
+            if (t + jumps[i] < t)
+                return fail(MTGP_EINVAL, "total jump of stream %u overflows 64 bits", ids[i]);
+            t += jumps[i];
+        }
+        // set index of each stream (per-stream parameter sets)
+        std::vector<uint32_t> set_of_stream;
+        std::vector<KSet> host_sets;
+        if (st->d_sets) {
+            set_of_stream.resize(st->n_streams);
+            host_sets.resize(st->n_sets);
+            J_TRY(cudaMemcpy(set_of_stream.data(), st->d_set_of, st->n_streams * 4, cudaMemcpyDeviceToHost),
+                  "cudaMemcpy(set index)");
+            J_TRY(cudaMemcpy(host_sets.data(), st->d_sets, st->n_sets * sizeof(KSet), cudaMemcpyDeviceToHost),
+                  "cudaMemcpy(parameter sets)");
+        }
+        std::vector<JumpItem> items;
+        std::vector<const Poly*> polys;
+        std::map<std::pair<uint32_t, uint64_t>, uint32_t> poly_index;
+        uint32_t max_deg = 0;
+        for (const auto& kv : total) {
+            if (kv.second == 0)
+                continue;
+            const uint32_t set = st->d_sets ? set_of_stream[kv.first] : 0u;
+            const auto pk = std::make_pair(set, kv.second);
+            auto pit = poly_index.find(pk);
+            if (pit == poly_index.end()) {
+                const SetP p = set_of(st->P.k, st->d_sets ? &host_sets[set] : nullptr);
+                const Poly* mu = cached_mu(p, st->P.d.mexp);
+                if (!mu)
+                    return fail(MTGP_EINVAL, "no annihilating polynomial found for parameter set %u", set);
+                const auto jk = std::make_pair(key_of(p), kv.second);
+                const Poly* gp = nullptr;
+                {
+                    std::lock_guard<std::mutex> g(g_cache_mutex);
+                    auto it = g_jump_cache.find(jk);
+                    if (it != g_jump_cache.end())
+                        gp = &it->second;
+                }
+                if (!gp) {
+                    Poly gpoly = pow_t_mod(kv.second - 1, *mu);
+                    if (degree(gpoly) < 0)
+                        gpoly.assign(1, 0);
+                    std::lock_guard<std::mutex> g(g_cache_mutex);
+                    gp = &g_jump_cache.emplace(jk, std::move(gpoly)).first->second;
+                }
+                pit = poly_index.emplace(pk, (uint32_t)polys.size()).first;
+                polys.push_back(gp);
+            }
+            const int d = std::max(degree(*polys[pit->second]), 0);
+            JumpItem ji;
+            ji.stream = kv.first;
+            ji.poly = pit->second;
+            ji.deg = (uint32_t)d;
+            ji.set = set;
+            items.push_back(ji);
+            max_deg = std::max(max_deg, (uint32_t)d);
+        }
+        if (items.empty())
+            return ok();
+        const uint32_t N = st->P.k.n;
+        const uint32_t poly_words = (max_deg + 1 + 31) / 32;
+        std::vector<uint32_t> pw(polys.size() * (size_t)poly_words, 0u);
+        for (size_t i = 0; i < polys.size(); ++i)
+            for (int k = 0; k <= degree(*polys[i]); ++k)
+                if (bit(*polys[i], (size_t)k))
+                    pw[i * poly_words + (size_t)k / 32] |= 1u << (k % 32);
+        // a zero g (possible only if t^(J-1) = 0 mod mu, which needs t | mu):
+        // the kernel then accumulates nothing and applies one step to 0
+        const size_t smem = ((size_t)max_deg + 1 + N - 1 + N) * 4;
+        int dev = 0, max_smem = 0;
+        J_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+        J_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+              "cudaDeviceGetAttribute");
+        if (smem + 64 > (size_t)max_smem)
+            return fail(MTGP_EINVAL, "state size too large for the jump kernel (%zu bytes of shared memory)", smem);
+        J_TRY(cudaFuncSetAttribute((const void*)mtgp_jump_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem), "cudaFuncSetAttribute");
+        cudaStream_t cs = (cudaStream_t)cuda_stream;
+        void *d_items = nullptr, *d_polys = nullptr;
+        J_TRY(cudaMallocAsync(&d_items, items.size() * sizeof(JumpItem), cs), "cudaMallocAsync");
+        cudaError_t e = cudaMallocAsync(&d_polys, pw.size() * 4, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(JumpItem), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_polys, pw.data(), pw.size() * 4, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) {
+            mtgp_jump_kernel<<<(unsigned)items.size(), 256, smem, cs>>>(st->P.k, st->d_states,
+                                                                        (const JumpItem*)d_items,
+                                                                        (const uint32_t*)d_polys, poly_words,
+                                                                        st->d_sets);
+            e = cudaGetLastError();
+        }
+        // the host arrays above are locals: wait for the copies before returning
+        const cudaError_t e2 = cudaStreamSynchronize(cs);
+        if (d_polys)
+            cudaFreeAsync(d_polys, cs);
+        cudaFreeAsync(d_items, cs);
+        if (e != cudaSuccess)
+            return fail_cuda(e, "jump kernel");
+        if (e2 != cudaSuccess)
+            return fail_cuda(e2, "cudaStreamSynchronize");
+        return ok();
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}

@@ -83,6 +83,8 @@ _SIGS = {
     "mtgp_params_get": [_VP, ctypes.POINTER(ParamsDesc)],
     "mtgp_params_free": [_VP],
     "mtgp_init_statuses": [_VP, _U32P, ctypes.c_uint32, _VP, ctypes.POINTER(_VP)],
+    "mtgp_jump": [_VP, _U32P, _U64P, ctypes.c_uint32, _VP],
+    "mtgp_params_minpoly": [_VP, _U64P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)],
     "mtgp_gap_histogram": [_VP, _U64P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                            _U64P, _VP],
     "mtgp_hamming_pairs": [_VP, _U64P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -534,3 +536,25 @@ def mtgp_hamming_pairs(values, counts, r=25, s=5, L=1200, bounds=(), stream=None
     _call("mtgp_hamming_pairs", _dev_ptr(values, int(counts.sum())), _p64(counts), counts.size, r, s, L,
           _p32(bnd) if bnd.size else None, bnd.size, _p64(table), _stream_handle(stream))
     return table
+
+
+# ---------------------------------------------------------------------------
+# Jump-ahead
+# ---------------------------------------------------------------------------
+def mtgp_jump(streams: Streams, stream_ids, jumps, stream=None):
+    """Advance each listed stream by its jump (numbers skipped, exactly)."""
+    ids = np.ascontiguousarray(stream_ids, dtype=np.uint32)
+    js = np.ascontiguousarray(jumps, dtype=np.uint64)
+    if ids.shape != js.shape or ids.ndim != 1:
+        raise ValueError("stream_ids and jumps must be 1-D arrays of the same length")
+    _call("mtgp_jump", streams.handle, _p32(ids), _p64(js), ids.size, _stream_handle(stream))
+
+
+def mtgp_params_minpoly(params: Params) -> np.ndarray:
+    """Coefficients (uint8, index = power of t) of the jump polynomial mu."""
+    d = ctypes.c_int32()
+    _call("mtgp_params_minpoly", params.handle, None, 0, ctypes.byref(d))
+    words = np.zeros(d.value // 64 + 1, dtype=np.uint64)
+    _call("mtgp_params_minpoly", params.handle, _p64(words), words.size, ctypes.byref(d))
+    bits = np.unpackbits(words.view(np.uint8), bitorder="little")
+    return bits[:d.value + 1].copy()
