@@ -485,8 +485,8 @@ def main():
                          "(skips autotuning)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--quality", action="store_true",
-                    help="also run the gap and Hamming-weight statistics over the generated output")
+    ap.add_argument("--no-quality", dest="quality", action="store_false",
+                    help="skip the gap and Hamming-weight statistics over the generated output")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
