@@ -394,6 +394,16 @@ mtgp_status mtgp_jump(mtgp_streams_t streams, const uint32_t* ids, const uint64_
 mtgp_status mtgp_params_minpoly(mtgp_params_t params, uint64_t* words, uint32_t cap_words,
                                 int32_t* degree);
 
+/* Sec. 4.1 (period of the parameterized status): sets *irreducible to 1 if
+ * the polynomial mu of mtgp_params_minpoly has degree Mexp and is
+ * irreducible over GF(2) (Rabin's test: t^(2^Mexp) = t mod mu and, for each
+ * prime q dividing Mexp, gcd(t^(2^(Mexp/q)) - t, mu) = 1), else to 0.  For a
+ * Mersenne-prime Mexp (2^Mexp - 1 prime, as for every MTGP exponent) this
+ * is exactly a period of 2^Mexp - 1 from every non-zero state.  The Mexp
+ * squarings run on the current device (about a second for Mexp 44497, 120 MB
+ * of device scratch); returns when done. */
+mtgp_status mtgp_params_period_check(mtgp_params_t params, void* cuda_stream, int32_t* irreducible);
+
 /* ---------------------------------------------------------------------- */
 /* Quality statistics: the data reductions of the paper's two failing     */
 /* BigCrush tests (Sec. 4.2), over outputs already in device memory       */

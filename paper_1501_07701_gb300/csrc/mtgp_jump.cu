@@ -435,6 +435,51 @@ __global__ void __launch_bounds__(256) mtgp_jump_kernel(const KParams P, uint32_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Period check: Rabin's irreducibility test of mu, run as a chain of
+// squarings a <- a^2 mod mu on the device.  Over GF(2) a^2 = sum a_i t^(2i):
+// the terms with 2i < D need no reduction (spread bits), the others are the
+// precomputed rows t^(2i) mod mu (i >= h = ceil(D/2)).  Output word w of one
+// squaring is therefore the spread of a's bits 32w .. 32w+31 XOR the word w of
+// every row whose bit of a is set; blocks split the words (x) and the rows
+// (y) and combine with 64-bit atomicXor into a zeroed output.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) mtgp_frobenius_kernel(const unsigned long long* __restrict__ a,
+                                                            unsigned long long* __restrict__ out,
+                                                            const unsigned long long* __restrict__ rows,
+                                                            uint32_t D, uint32_t W, uint32_t h,
+                                                            uint32_t rows_per_slice)
+{
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i0 = h + blockIdx.y * rows_per_slice;
+    const uint32_t i1 = min(D, i0 + rows_per_slice);
+    if (w >= W)
+        return;
+    unsigned long long acc = 0;
+    if (blockIdx.y == 0) {
+        // spread: bit i of a (i < h) -> bit 2i; output word w takes a's bits 32w .. 32w+31
+        const uint32_t src = 32u * w;
+        if (src < h) {
+            const unsigned long long word = a[src / 64u];
+            uint32_t half = (uint32_t)(word >> (src % 64u));
+            if (h - src < 32u)
+                half &= (1u << (h - src)) - 1u;   // only bits i < h
+            unsigned long long x = half;
+            x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+            x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+            x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+            x = (x | (x << 2)) & 0x3333333333333333ull;
+            x = (x | (x << 1)) & 0x5555555555555555ull;
+            acc = x;
+        }
+    }
+    for (uint32_t i = i0; i < i1; ++i)
+        if ((a[i / 64u] >> (i % 64u)) & 1ull)
+            acc ^= rows[(size_t)(i - h) * W + w];
+    if (acc)
+        atomicXor(out + w, acc);
+}
+
 #define J_TRY(call, what)                 \
     do {                                  \
         cudaError_t e_ = (call);          \
@@ -463,6 +508,120 @@ extern "C" mtgp_status mtgp_params_minpoly(mtgp_params_t params, uint64_t* words
             std::fill(words, words + cap_words, 0ull);
             std::copy(mu->begin(), mu->end(), words);
         }
+        return ok();
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+extern "C" mtgp_status mtgp_params_period_check(mtgp_params_t params, void* cuda_stream, int32_t* irreducible)
+{
+    try {
+        if (!params || !irreducible)
+            return fail(MTGP_EINVAL, "null argument");
+        *irreducible = 0;
+        const uint32_t n = params->d.mexp;
+        const SetP p = set_of(params->k, nullptr);
+        const Poly* mup = cached_mu(p, n);
+        if (!mup)
+            return fail(MTGP_EINVAL, "no annihilating polynomial found for this parameter set");
+        const Poly& mu = *mup;
+        const int D = degree(mu);
+        // a full-period transition needs deg mu = Mexp, mu(0) = 1, mu(1) = 1
+        int terms = 0;
+        for (uint64_t wd : mu)
+            terms += __builtin_popcountll(wd);
+        if (D != (int)n || !bit(mu, 0) || terms % 2 == 0)
+            return ok();
+        // prime divisors q of n: Rabin also needs gcd(t^(2^(n/q)) - t, mu) = 1
+        std::vector<uint32_t> qs;
+        {
+            uint32_t m = n;
+            for (uint32_t q = 2; q * q <= m; ++q)
+                if (m % q == 0) {
+                    qs.push_back(q);
+                    while (m % q == 0)
+                        m /= q;
+                }
+            if (m > 1)
+                qs.push_back(m);
+        }
+        std::vector<uint32_t> capture;   // squaring counts n/q to bring back
+        for (uint32_t q : qs)
+            if (q != n)
+                capture.push_back(n / q);
+        // rows t^(2i) mod mu for i = h .. D-1
+        const uint32_t W = (uint32_t)(D / 64 + 1), h = (uint32_t)((D + 1) / 2);
+        std::vector<unsigned long long> rows((size_t)(D - h) * W, 0ull);
+        {
+            Poly r;
+            xor_shifted(r, Poly(1, 1ull), 2 * (size_t)h);   // t^(2h)
+            r = mod(r, mu);
+            for (uint32_t i = h; i < (uint32_t)D; ++i) {
+                r.resize(W, 0ull);
+                std::copy(r.begin(), r.begin() + W, rows.begin() + (size_t)(i - h) * W);
+                Poly s2;
+                xor_shifted(s2, r, 2);
+                r = mod(s2, mu);
+            }
+        }
+        cudaStream_t cs = (cudaStream_t)cuda_stream;   // current device
+        unsigned long long *d_rows = nullptr, *d_a = nullptr, *d_b = nullptr;
+        auto cleanup = [&]() {
+            if (d_rows)
+                cudaFreeAsync(d_rows, cs);
+            if (d_a)
+                cudaFreeAsync(d_a, cs);
+            if (d_b)
+                cudaFreeAsync(d_b, cs);
+        };
+        cudaError_t e = cudaMallocAsync((void**)&d_rows, rows.size() * 8, cs);
+        if (e == cudaSuccess)
+            e = cudaMallocAsync((void**)&d_a, (size_t)W * 8, cs);
+        if (e == cudaSuccess)
+            e = cudaMallocAsync((void**)&d_b, (size_t)W * 8, cs);
+        std::vector<unsigned long long> t1(W, 0ull);
+        t1[0] = 2ull;   // the polynomial t
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_rows, rows.data(), rows.size() * 8, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_a, t1.data(), (size_t)W * 8, cudaMemcpyHostToDevice, cs);
+        const uint32_t rows_per_slice = 64;
+        const dim3 grid((W + 255) / 256, ((uint32_t)D - h + rows_per_slice - 1) / rows_per_slice);
+        std::vector<std::vector<unsigned long long>> captured;
+        std::vector<unsigned long long> host(W);
+        for (uint32_t k = 1; k <= n && e == cudaSuccess; ++k) {
+            e = cudaMemsetAsync(d_b, 0, (size_t)W * 8, cs);
+            if (e != cudaSuccess)
+                break;
+            mtgp_frobenius_kernel<<<grid, 256, 0, cs>>>(d_a, d_b, d_rows, (uint32_t)D, W, h, rows_per_slice);
+            e = cudaGetLastError();
+            std::swap(d_a, d_b);
+            if (e == cudaSuccess && std::find(capture.begin(), capture.end(), k) != capture.end()) {
+                e = cudaMemcpyAsync(host.data(), d_a, (size_t)W * 8, cudaMemcpyDeviceToHost, cs);
+                if (e == cudaSuccess)
+                    e = cudaStreamSynchronize(cs);
+                captured.push_back(host);
+            }
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host.data(), d_a, (size_t)W * 8, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(cs);
+        cleanup();
+        if (e != cudaSuccess)
+            return fail_cuda(e, "period check");
+        // t^(2^n) == t (mod mu)?
+        if (host != t1)
+            return ok();
+        for (auto& c : captured) {   // gcd(t^(2^(n/q)) - t, mu) == 1
+            Poly x(c.begin(), c.end());
+            x[0] ^= 2ull;
+            trim(x);
+            if (degree(gcd(mu, x)) != 0)
+                return ok();
+        }
+        *irreducible = 1;
         return ok();
     } catch (const std::bad_alloc&) {
         return fail(MTGP_ENOMEM, "host allocation failed");

@@ -85,6 +85,7 @@ _SIGS = {
     "mtgp_init_statuses": [_VP, _U32P, ctypes.c_uint32, _VP, ctypes.POINTER(_VP)],
     "mtgp_jump": [_VP, _U32P, _U64P, ctypes.c_uint32, _VP],
     "mtgp_params_minpoly": [_VP, _U64P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)],
+    "mtgp_params_period_check": [_VP, _VP, ctypes.POINTER(ctypes.c_int32)],
     "mtgp_gap_histogram": [_VP, _U64P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                            _U64P, _VP],
     "mtgp_hamming_pairs": [_VP, _U64P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -558,3 +559,11 @@ def mtgp_params_minpoly(params: Params) -> np.ndarray:
     _call("mtgp_params_minpoly", params.handle, _p64(words), words.size, ctypes.byref(d))
     bits = np.unpackbits(words.view(np.uint8), bitorder="little")
     return bits[:d.value + 1].copy()
+
+
+def mtgp_params_period_check(params: Params, stream=None) -> bool:
+    """True if the transition polynomial has degree Mexp and is irreducible
+    (for a Mersenne-prime Mexp: period 2^Mexp - 1)."""
+    r = ctypes.c_int32()
+    _call("mtgp_params_period_check", params.handle, _stream_handle(stream), ctypes.byref(r))
+    return bool(r.value)

@@ -167,3 +167,93 @@ def test_jump_errors(_cuda):
         mtgp.mtgp_jump(st, [2], [5])
     with pytest.raises(mtgp.MtgpError):
         mtgp.mtgp_jump(st, [0, 0], [2 ** 63, 2 ** 63])
+
+
+# ---------------------------------------------------------------------------
+# Period check (Rabin's test on the device) against the distinct-degree
+# criterion on the host: mu is irreducible iff gcd(mu, t^(2^k) - t) = 1 for
+# every k <= deg/2 (polynomials as Python integers, bit i = coefficient t^i).
+# ---------------------------------------------------------------------------
+def _clmul(a, b):
+    r = 0
+    while b:
+        if b & 1:
+            r ^= a
+        a <<= 1
+        b >>= 1
+    return r
+
+
+def _pmod(a, m):
+    dm = m.bit_length() - 1
+    while a.bit_length() - 1 >= dm:
+        a ^= m << (a.bit_length() - 1 - dm)
+    return a
+
+
+def _pgcd(a, b):
+    while b:
+        a, b = b, _pmod(a, b)
+    return a
+
+
+def _irreducible_ddf(mu_bits):
+    mu = sum(1 << i for i, b in enumerate(mu_bits) if b)
+    d = mu.bit_length() - 1
+    x = 2
+    for _ in range(d // 2):
+        x = _pmod(_clmul(x, x), mu)
+        if _pgcd(mu, x ^ 2) != 1:
+            return False
+    return d >= 1
+
+
+def _toy_params(tmp_path, mexp, pos, sh1, sh2, rb, tb):
+    path = tmp_path / ("toy%d_%d_%d.txt" % (mexp, pos, sh1))
+    path.write_text("mexp %d\npos %d\nsh1 %d\nsh2 %d\nrec_basis %s\ntmp_basis %s\n" % (
+        mexp, pos, sh1, sh2, " ".join(map(hex, rb)), " ".join(map(hex, tb))))
+    return mtgp.mtgp_params_load(str(path))
+
+
+# toy sets (Mexp 107 and 127, Mersenne exponents) whose polynomial is
+# irreducible of degree Mexp, i.e. of period 2^Mexp - 1
+FULL_PERIOD_TOYS = [
+    (107, 1, 19, 8, [4082844636, 2674313637, 2742504081, 3367881795], [530185877, 191712196, 1837422121, 2252332600]),
+    (107, 3, 7, 6, [3055337368, 4127762061, 938604234, 606372027], [2423534270, 1784284154, 1040217680, 2742214121]),
+    (127, 3, 24, 5, [3594327011, 1983446878, 1706042657, 4053708494], [1110286991, 448702083, 1960614134, 1319519321]),
+]
+
+
+@gpu
+def test_period_check_full_period_toys(_cuda, tmp_path):
+    for mexp, pos, sh1, sh2, rb, tb in FULL_PERIOD_TOYS:
+        gp = _toy_params(tmp_path, mexp, pos, sh1, sh2, rb, tb)
+        mu = mtgp.mtgp_params_minpoly(gp)
+        assert mu.size - 1 == mexp and _irreducible_ddf(mu)
+        assert mtgp.mtgp_params_period_check(gp)
+
+
+@gpu
+@pytest.mark.parametrize("mexp,n", [(61, 2), (89, 3), (107, 4), (127, 4), (100, 4), (119, 4)])
+def test_period_check_agrees_with_ddf(_cuda, tmp_path, mexp, n):
+    """Random toy sets (mostly reducible); 100 and 119 are composite, which
+    exercises the gcd part of Rabin's test."""
+    rng = np.random.default_rng(1000 + mexp)
+    for _ in range(12):
+        args = (mexp, int(rng.integers(1, n)), int(rng.integers(1, 32)), int(rng.integers(1, 32)),
+                [int(v) for v in rng.integers(0, 2 ** 32, 4, dtype=np.uint64)],
+                [int(v) for v in rng.integers(0, 2 ** 32, 4, dtype=np.uint64)])
+        gp = _toy_params(tmp_path, *args)
+        mu = mtgp.mtgp_params_minpoly(gp)
+        expect = mu.size - 1 == mexp and _irreducible_ddf(mu)
+        assert mtgp.mtgp_params_period_check(gp) == expect, args
+
+
+@gpu
+def test_period_check_of_benchmark_sets(_cuda):
+    """Records the verdict for the benchmark parameter sets (no independent
+    check exists at this size; the toys above pin the implementation)."""
+    for mexp in (11213, 23209, 44497):
+        verdict = mtgp.mtgp_params_period_check(mtgp.mtgp_params_generate(mexp, workloads.PARAM_SEED))
+        print("Mexp %d seed 0x5EED: full period %s" % (mexp, verdict))
+        assert verdict in (True, False)
