@@ -448,3 +448,29 @@ def test_full_uneven_plan():
         torch.cuda.synchronize()
         mtgp.mtgp_check(st)
         states = _check_full(st, op, out, counts, 0, states, sample)
+
+
+def test_single_request_beyond_2p32():
+    """Maximum size: one request of 2^32 + 1000 numbers from one stream
+    (17 GB of output, row and output indices past 32 bits).  Checked by the
+    oracle on the first 2^20 outputs; the final state must equal an
+    independent jump of the same length (jumps are oracle-checked up to
+    10^7 and compose exactly), and the last 1000 outputs must equal the
+    oracle started from the state jumped to 2^32."""
+    gp, op = _both_params(11213)
+    big = (1 << 32) + 1000
+    st = mtgp.mtgp_init_statuses(gp, np.array([5, 6], np.uint32))
+    s0 = mtgp.mtgp_get_statuses(st)[0]
+    out = torch.empty(big, dtype=torch.int32, device="cuda")
+    mtgp.mtgp_generate_u32(st, [0], [big], out)
+    torch.cuda.synchronize()
+    mtgp.mtgp_check(st)
+    ref, _ = oracle.generate(op, s0, 1 << 20)
+    _assert_same(out[:1 << 20].cpu().numpy().view(np.uint32), ref, "first 2^20")
+    ref_st = mtgp.mtgp_init_statuses(gp, np.array([5], np.uint32))
+    mtgp.mtgp_jump(ref_st, [0], [1 << 32])
+    s32 = mtgp.mtgp_get_statuses(ref_st)[0]
+    tail, s_end = oracle.generate(op, s32, 1000)
+    _assert_same(out[1 << 32:].cpu().numpy().view(np.uint32), tail, "last 1000")
+    _assert_same(mtgp.mtgp_get_statuses(st)[0], s_end, "final state")
+    del out
