@@ -368,7 +368,7 @@ mtgp_status mtgp_server_run_trace(mtgp_server_t server, const double* t_arrival,
 mtgp_status mtgp_server_free(mtgp_server_t server);
 
 /* ---------------------------------------------------------------------- */
-/* Jump-ahead (sub-streams of one generator, Sec. 2)                      */
+/* Jump-ahead (sub-streams of one generator, Sec. 1)                      */
 /* ---------------------------------------------------------------------- */
 
 /* Advances stream ids[i] by jumps[i] numbers, exactly as generating and

@@ -1,6 +1,6 @@
 // Jump-ahead: advance streams by J numbers without producing them.
 //
-// The paper motivates splitting one generator into sub-streams (Sec. 2); for
+// The paper raises distributing streams across a machine (Sec. 1); for
 // an F2-linear generator the exact way is a polynomial jump.  The state of a
 // stream is the window w = (x_c .. x_{c+N-1}); one step F maps it to
 // (x_{c+1} .. x_{c+N}).  F is linear over GF(2).  Its kernel K holds the
