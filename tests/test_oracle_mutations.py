@@ -12,7 +12,6 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "mtgp_oracle.c")
 
 MUTANTS = {
     "successor_index": ("uint32_t y = (x[i] & p->mask) ^ x[i + 1];",
@@ -55,15 +54,41 @@ QUALITY_MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(QUALITY_MUTANTS))
-def test_pins_reject_planted_mistake(name, tmp_path):
-    if name in MUTANTS:
-        before, after = MUTANTS[name]
-        pins = "test_oracle_pins.py"
-    else:
-        before, after = (x.replace("\\n", "\n") for x in QUALITY_MUTANTS[name])
-        pins = "test_quality_oracle.py"
-    src = open(SRC).read()
+# Mistakes in the original-MT oracle (the comparison generator of Sec. 5.3).
+MT_MUTANTS = {
+    "mt_successor_index": ("(x[k + 1] & lower)", "(x[k + 2] & lower)"),
+    "mt_middle_index": ("x[k + n] = x[k + q->m] ^ ya;", "x[k + n] = x[k + q->m - 1] ^ ya;"),
+    "mt_upper_lower_swapped": ("uint32_t y = (x[k] & upper) | (x[k + 1] & lower);",
+                               "uint32_t y = (x[k] & lower) | (x[k + 1] & upper);"),
+    "mt_twist_test_bit": ("((y & 1u) ? q->a : 0u)", "((y & 2u) ? q->a : 0u)"),
+    "mt_twist_shift_direction": ("uint32_t ya = (y >> 1)", "uint32_t ya = (y << 1)"),
+    "mt_separation_width": ("0xFFFFFFFFu << q->r : 0xFFFFFFFFu;",
+                            "0xFFFFFFFFu << (q->r - 1u) : 0xFFFFFFFFu;"),
+    "mt_temper_b_direction": ("z ^= (z << q->s) & q->b;", "z ^= (z >> q->s) & q->b;"),
+    "mt_temper_c_mask": ("z ^= (z << q->t) & q->c;", "z ^= (z << q->t) & q->b;"),
+    "mt_temper_last_shift": ("z ^= z >> q->l;", "z ^= z >> q->u;"),
+    "mt_temper_before_twist": ("uint32_t z = x[k + n];", "uint32_t z = x[k + q->m];"),
+    "mt_seed_multiplier": ("1812433253u * (state[i - 1]", "1812433255u * (state[i - 1]"),
+    "mt_state_save_offset": ("memcpy(state, x + count, (size_t)n * sizeof(uint32_t));",
+                             "memcpy(state, x + count + 1, (size_t)(n - 1) * sizeof(uint32_t));"),
+    "mt_middle_draw": ("q->m = q->n / 2u;", "q->m = (q->n + 1u) / 2u;"),
+    "mt_a_top_bit": ("| 0x80000000u;", "| 0x40000000u;"),
+}
+
+# group -> (oracle source, library override variable, pin suite, mutants)
+GROUPS = {
+    "mtgp": ("mtgp_oracle.c", "MTGP_ORACLE_LIB", "test_oracle_pins.py", MUTANTS),
+    "quality": ("mtgp_oracle.c", "MTGP_ORACLE_LIB", "test_quality_oracle.py", QUALITY_MUTANTS),
+    "mt": ("mt_oracle.c", "MT_ORACLE_LIB", "test_mt_oracle.py", MT_MUTANTS),
+}
+CASES = [(g, name) for g in GROUPS for name in sorted(GROUPS[g][3])]
+
+
+@pytest.mark.parametrize("group,name", CASES, ids=["%s-%s" % c for c in CASES])
+def test_pins_reject_planted_mistake(group, name, tmp_path):
+    src_name, env_var, pins, mutants = GROUPS[group]
+    before, after = (x.replace("\\n", "\n") for x in mutants[name])
+    src = open(os.path.join(ROOT, "oracle", src_name)).read()
     assert src.count(before) == 1, name
     mutant_c = tmp_path / "mutant.c"
     mutant_c.write_text(src.replace(before, after))
@@ -72,7 +97,7 @@ def test_pins_reject_planted_mistake(name, tmp_path):
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-shared", "-fPIC",
                            "-I", os.path.join(ROOT, "oracle"), "-o", str(lib), str(mutant_c),
                            "-lpthread"])
-    env = dict(os.environ, MTGP_ORACLE_LIB=str(lib))
+    env = dict(os.environ, **{env_var: str(lib)})
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
