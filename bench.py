@@ -69,23 +69,26 @@ def recorded_traffic(kernel: str, workload_name: str):
     return float(m_b.group(1))
 
 
-def workload(name: str, rank: int, streams: int = 0, count: int = 0, param_sets: int = 0):
+def workload(name: str, rank: int, streams: int = 0, count: int = 0, param_sets: int = 0,
+             generator: str = ""):
+    """Seeds and counts of a named workload; `generator` replaces the MTGP32
+    label in the description (the comparison generator runs the same shapes)."""
+    gen = generator or "MTGP32 Mexp 11213"
     if name == "uneven":
         w = workloads.uneven()
-        desc = ("uneven: 10000 MTGP32 Mexp 11213 streams, counts floor(2^U), U~U[10,22] "
-                "(seed 7)")
+        desc = "uneven: 10000 %s streams, counts floor(2^U), U~U[10,22] (seed 7)" % gen
         if streams:
             w = {"mexp": w["mexp"], "seeds": w["seeds"][:streams], "counts": w["counts"][:streams]}
-            desc = "uneven subset: first %d of the 10000 streams" % streams
+            desc = "uneven subset: first %d of the 10000 %s streams" % (streams, gen)
     elif name == "single":
         w = workloads.single()
-        desc = "single: 1 MTGP32 Mexp 11213 stream (seed 1) x 2^20"
+        desc = "single: 1 %s stream (seed 1) x 2^20" % gen
     elif name == "equal":
         w = workloads.equal(streams or 4096, count or (1 << 18))
-        desc = "equal: %d MTGP32 Mexp 11213 streams x %d" % (streams or 4096, count or (1 << 18))
+        desc = "equal: %d %s streams x %d" % (streams or 4096, gen, count or (1 << 18))
     elif name.startswith("long"):
         w = workloads.long_streams(int(name[4:]))
-        desc = "long: 1024 MTGP32 Mexp %s streams x 2^20" % name[4:]
+        desc = "long: 1024 %s streams x 2^20" % (generator or "MTGP32 Mexp " + name[4:])
     else:
         raise SystemExit("unknown workload " + name)
     w["seeds"] = mdist.weak_seeds(w["seeds"], rank)
@@ -163,15 +166,21 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 26, seed=0):
+def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 26, seed=0, mt_params=None):
     """Times the CPU oracle on a bounded random sample of the workload's
     streams: whole streams in random order, in batches of at most max_batch
     numbers (outputs discarded batch by batch), until budget_s seconds of
     oracle time have been spent.  Returns (numbers/s, numbers, seconds,
-    streams)."""
+    streams).  With mt_params (an oracle.mt parameter set) the original-MT
+    oracle is timed instead."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
-    p_of = oracle_params_of(w)
+    if mt_params is not None:
+        import oracle.mt as gen_oracle
+        p_of = lambda s: mt_params  # noqa: E731
+    else:
+        gen_oracle = oracle
+        p_of = oracle_params_of(w)
     per_stream = w.get("param_seeds") is not None
     pool = ThreadPoolExecutor(threads) if per_stream else None
     order = np.random.default_rng(seed).permutation(w["seeds"].size)
@@ -183,14 +192,14 @@ def oracle_rate(w, budget_s: float, threads: int, max_batch=1 << 26, seed=0):
             batch.append(int(order[k]))
             acc += int(w["counts"][order[k]])
             k += 1
-        states = [oracle.init_state(p_of(i), int(w["seeds"][i])) for i in batch]
+        states = [gen_oracle.init_state(p_of(i), int(w["seeds"][i])) for i in batch]
         t0 = time.perf_counter()
         if per_stream:   # each stream with its own set, streams spread over the host threads
             list(pool.map(lambda a: oracle.generate(p_of(a[0]), a[1], int(w["counts"][a[0]])),
                           zip(batch, states)))
         else:
-            oracle.generate_many(p_of(0), np.stack(states), np.arange(len(batch)), w["counts"][batch],
-                                 0, threads)
+            gen_oracle.generate_many(p_of(0), np.stack(states), np.arange(len(batch)),
+                                     w["counts"][batch], 0, threads)
         t_all += time.perf_counter() - t0
         done += acc
         used += len(batch)
@@ -310,14 +319,7 @@ def run_ours(args, rank, world, local_rank):
     value = numbers_all / elapsed / 1e9
 
     # roofline of the dominant kernel (the persistent generation kernel)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
+    peak, peak_src = hbm_peak()
     n_words = mtgp.mtgp_streams_info(st)[1]
     alg_bytes = 4.0 * total + 8.0 * n_words * info["n_items"]
     kern_avg = sum(kern_ms) / len(kern_ms) / 1e3
@@ -328,21 +330,7 @@ def run_ours(args, rank, world, local_rank):
     # taken before the bandwidth check below overwrites the buffer
     qual = None
     if rank == 0 and args.quality:
-        from paper_1501_07701_gb300 import quality
-        bounds = quality.default_hamming_bounds(1200, 4)
-        q0, q1, q2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        q0.record(stream)
-        hist = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128, stream=stream)
-        q1.record(stream)
-        tab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds, stream=stream)
-        q2.record(stream)
-        stream.synchronize()
-        g = quality.gap_test(hist.sum(axis=0), b=5)
-        hm = quality.hamming_test(tab.sum(axis=0), L=1200, bounds=bounds)
-        qual = {"gap_test": {"r": 25, "beta": "1/32", "t": 128, "gnum_s": total / (q0.elapsed_time(q1) * 1e6),
-                             "pooled": g},
-                "hamming_indep": {"r": 25, "s": 5, "L": 1200, "classes": len(bounds) + 1,
-                                  "gnum_s": total / (q1.elapsed_time(q2) * 1e6), "pooled": hm}}
+        qual = quality_stats(mtgp, torch, out, counts, stream)
 
     # self-measured write-only bandwidth (fill of the output buffer)
     wb_a, wb_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -401,6 +389,139 @@ def run_ours(args, rank, world, local_rank):
             "serving": serving,
             "quality": qual,
             "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def hbm_peak():
+    """The measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), else the
+    6.8 TB/s fallback; returns (GB/s, "measured" | "fallback")."""
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
+    except (OSError, ValueError):
+        peak = None
+    return (peak, "measured") if peak else (6800.0, "fallback")
+
+
+def quality_stats(mtgp, torch, out, counts, stream):
+    """Pooled statistics of tests 35 and 100 (Sec. 4.2) over a launch's
+    output, with the rate of each reduction kernel."""
+    from paper_1501_07701_gb300 import quality
+    total = int(counts.sum())
+    bounds = quality.default_hamming_bounds(1200, 4)
+    q0, q1, q2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    q0.record(stream)
+    hist = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128, stream=stream)
+    q1.record(stream)
+    tab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds, stream=stream)
+    q2.record(stream)
+    stream.synchronize()
+    g = quality.gap_test(hist.sum(axis=0), b=5)
+    hm = quality.hamming_test(tab.sum(axis=0), L=1200, bounds=bounds)
+    return {"gap_test": {"r": 25, "beta": "1/32", "t": 128,
+                         "gnum_s": total / (q0.elapsed_time(q1) * 1e6), "pooled": g},
+            "hamming_indep": {"r": 25, "s": 5, "L": 1200, "classes": len(bounds) + 1,
+                              "gnum_s": total / (q1.elapsed_time(q2) * 1e6), "pooled": hm}}
+
+
+def run_mt(args, rank, world, local_rank):
+    """The comparison generator of Sec. 5.3 (the original Mersenne Twister)
+    on the same workload shapes: one mtgp_mt_generate launch per step."""
+    import torch
+    import oracle.mt as omt
+    from paper_1501_07701_gb300 import mtgp
+    from paper_1501_07701_gb300.build import build
+    build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if args.mt_p == 19937:
+        q, oq, label = mtgp.mtgp_mt_params_mt19937(), omt.params_mt19937(), "MT19937"
+    else:
+        q = mtgp.mtgp_mt_params_generate(args.mt_p, workloads.PARAM_SEED)
+        oq = omt.params_generate(args.mt_p, workloads.PARAM_SEED)
+        label = "original-MT p %d (seed-generated set)" % args.mt_p
+    w, desc = workload(args.workload, rank, args.streams, args.count, generator=label)
+    counts = w["counts"]
+    total = int(counts.sum())
+    stream = torch.cuda.Stream()
+    mt = mtgp.mtgp_mt_init(q, w["seeds"], stream)
+    out = torch.empty(total, dtype=torch.int32, device=dev)
+    ids = np.arange(w["seeds"].size, dtype=np.uint32)
+    fmt = FORMATS[args.format]
+    bit_exact = None
+    states0 = mtgp.mtgp_mt_get_statuses(mt, stream) if rank == 0 else None
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MiB > L2
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            mtgp.mtgp_mt_generate(mt, ids, counts, fmt, out, stream)
+            if i == 0 and rank == 0:
+                stream.synchronize()
+                offs = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
+                bit_exact = True
+                for s in sorted({int(np.argmax(counts)), 0, counts.size - 1, counts.size // 2}):
+                    ref, _ = omt.generate(oq, states0[s], int(counts[s]), fmt)
+                    got = out[int(offs[s]):int(offs[s + 1])].cpu().numpy().view(np.uint32)
+                    bit_exact = bit_exact and bool(np.array_equal(ref, got))
+            flush.fill_(1)
+    mtgp.mtgp_mt_check(mt, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clocks = ClockSampler(cvd.split(",")[local_rank] if cvd else str(local_rank))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            mtgp.mtgp_mt_generate(mt, ids, counts, fmt, out, stream)
+            ev[i][1].record(stream)
+            flush.fill_(i)
+    t1.record(stream)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = mdist.max_over_ranks(t0.elapsed_time(t1) / 1e3, device=dev)
+    kern_avg = sum(a.elapsed_time(b) for a, b in ev) / len(ev) / 1e3
+    value = total * args.steps * world / elapsed / 1e9
+    peak, peak_src = hbm_peak()
+    alg_bytes = 4.0 * total + 8.0 * oq.n * ids.size
+    achieved = alg_bytes / kern_avg / 1e9
+    qual = quality_stats(mtgp, torch, out, counts, stream) if rank == 0 and args.quality else None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r, n, t, ns = oracle_rate(w, args.cpu_seconds, threads, mt_params=oq)
+        cpu = {"value": r / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d random whole streams of the workload, %d numbers, %.1f s" % (ns, n, t)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "generator": label, "params": oq.as_dict(),
+            "config": {"workload": desc, "numbers_per_step_per_gpu": total, "format": args.format,
+                       "l2": "output > 129 MB L2 plus a 256 MiB rewrite between timed steps",
+                       "launch": "mtgp_mt_generate per step (work table upload + one kernel)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel_ms_avg": 1e3 * kern_avg, "kernel": "mt_gen_kernel"},
+            "clocks": clk, "e2e": None, "gpu_launches": args.steps,
+            "bit_exact_sample": bit_exact, "quality": qual, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -489,6 +610,10 @@ def main():
     ap.add_argument("--no-quality", dest="quality", action="store_false",
                     help="skip the gap and Hamming-weight statistics over the generated output")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--generator", default="mtgp", choices=["mtgp", "mt"],
+                    help="mt: the original Mersenne Twister of Sec. 5.3 on the same workload")
+    ap.add_argument("--mt-p", type=int, default=3217,
+                    help="exponent of the original-MT set (19937 = MT19937, else seed-generated)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -499,6 +624,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.generator == "mt":
+        run_mt(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -80,6 +80,13 @@ __host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return 32u + (
 // shifts are in 1..31.
 bool fast_supported(const KParams& P, int k, int g = 4);
 
+// Lets `fn` launch with up to the device's opt-in maximum of dynamic shared
+// memory (cudaErrorInvalidValue if `need` exceeds it).  The limit is a
+// process-wide attribute of the function, so it is always raised to that
+// maximum: a per-handle value could lower it under another live handle.
+// Occupancy still follows each launch's own size.
+cudaError_t allow_max_dynamic_smem(const void* fn, int device, size_t need);
+
 // Seed status -> state rows (row stride P.np words; padding words zeroed).
 cudaError_t launch_init(const KParams& P, const uint32_t* d_seeds, uint32_t n_streams,
                         uint32_t* d_states, cudaStream_t s);

@@ -175,6 +175,17 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
 // ---------------------------------------------------------------------------
 // Geometry and dispatch
 // ---------------------------------------------------------------------------
+cudaError_t allow_max_dynamic_smem(const void* fn, int device, size_t need)
+{
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess)
+        return e;
+    if (need > (size_t)optin)
+        return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 static int fast_m(const KParams& P) { return (int)((P.n + 31u) / 32u); }
 
 bool fast_supported(const KParams& P, int k, int g)
@@ -221,11 +232,8 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
         fn = (const void*)mtgp_ring_kernel;
     }
     cudaError_t e;
-    if (g->smem > 48u * 1024u) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem);
-        if (e != cudaSuccess)
-            return e;
-    }
+    if (g->smem > 48u * 1024u && (e = allow_max_dynamic_smem(fn, device, g->smem)) != cudaSuccess)
+        return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g->threads, g->smem);
     if (e != cudaSuccess)

@@ -54,6 +54,14 @@ class PlanInfo(ctypes.Structure):
                 ("regs_per_thread", ctypes.c_uint32), ("resident_ctas_per_sm", ctypes.c_uint32)]
 
 
+class MtParams(ctypes.Structure):
+    """mtgp_mt_params (include/mtgp_mt.h)."""
+    _fields_ = [(f, ctypes.c_uint32) for f in ("p", "n", "m", "r", "a", "u", "s", "t", "l", "b", "c")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("max_tick_requests", ctypes.c_uint32)]
@@ -124,6 +132,14 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_uint32,
                               ctypes.POINTER(ctypes.c_double), _U64P, ctypes.POINTER(ServerStats)],
     "mtgp_server_free": [_VP],
+    "mtgp_mt_params_mt19937": [ctypes.POINTER(MtParams)],
+    "mtgp_mt_params_generate": [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(MtParams)],
+    "mtgp_mt_init": [ctypes.POINTER(MtParams), _U32P, ctypes.c_uint32, _VP, ctypes.POINTER(_VP)],
+    "mtgp_mt_set_statuses": [_VP, _U32P, _VP],
+    "mtgp_mt_get_statuses": [_VP, _U32P, _VP],
+    "mtgp_mt_generate": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP, _VP],
+    "mtgp_mt_check": [_VP, _VP],
+    "mtgp_mt_free": [_VP],
     "mtgp_last_error": [],
     "mtgp_version": [],
 }
@@ -567,3 +583,71 @@ def mtgp_params_period_check(params: Params, stream=None) -> bool:
     r = ctypes.c_int32()
     _call("mtgp_params_period_check", params.handle, _stream_handle(stream), ctypes.byref(r))
     return bool(r.value)
+
+
+# ---------------------------------------------------------------------------
+# The original Mersenne Twister (comparison generator, include/mtgp_mt.h)
+# ---------------------------------------------------------------------------
+class MtStreams:
+    """Owning wrapper of an mtgp_mt_t."""
+
+    def __init__(self, handle, params: MtParams, n_streams: int):
+        self.handle = handle
+        self.params = params
+        self.n_streams = n_streams
+
+    def close(self):
+        if self.handle:
+            _call("mtgp_mt_free", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mtgp_mt_params_mt19937() -> MtParams:
+    q = MtParams()
+    _call("mtgp_mt_params_mt19937", ctypes.byref(q))
+    return q
+
+
+def mtgp_mt_params_generate(p: int, seed: int) -> MtParams:
+    q = MtParams()
+    _call("mtgp_mt_params_generate", p, seed, ctypes.byref(q))
+    return q
+
+
+def mtgp_mt_init(params: MtParams, seeds, stream=None) -> MtStreams:
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+    h = _VP()
+    q = MtParams(*[getattr(params, f) for f, _ in MtParams._fields_])
+    _call("mtgp_mt_init", ctypes.byref(q), _p32(seeds), seeds.size, _stream_handle(stream),
+          ctypes.byref(h))
+    return MtStreams(h, q, seeds.size)
+
+
+def mtgp_mt_set_statuses(mt: MtStreams, states, stream=None):
+    states = np.ascontiguousarray(states, dtype=np.uint32)
+    if states.shape != (mt.n_streams, mt.params.n):
+        raise ValueError("states must have shape (%d, %d)" % (mt.n_streams, mt.params.n))
+    _call("mtgp_mt_set_statuses", mt.handle, _p32(states), _stream_handle(stream))
+
+
+def mtgp_mt_get_statuses(mt: MtStreams, stream=None) -> np.ndarray:
+    out = np.zeros((mt.n_streams, mt.params.n), np.uint32)
+    _call("mtgp_mt_get_statuses", mt.handle, _p32(out), _stream_handle(stream))
+    return out
+
+
+def mtgp_mt_generate(mt: MtStreams, stream_ids, counts, fmt, out, stream=None):
+    ids, counts = _req_arrays(stream_ids, counts)
+    total = int(counts.sum()) if counts.size else 0
+    _call("mtgp_mt_generate", mt.handle, _p32(ids), _p64(counts), ids.size, int(fmt),
+          _dev_ptr(out, total), _stream_handle(stream))
+
+
+def mtgp_mt_check(mt: MtStreams, stream=None):
+    _call("mtgp_mt_check", mt.handle, _stream_handle(stream))

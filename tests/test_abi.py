@@ -114,3 +114,23 @@ def test_last_error_is_thread_local_message(lib):
     with pytest.raises(mtgp.MtgpError) as ei:
         mtgp.mtgp_params_generate(64, 1)
     assert "64" in str(ei.value)
+
+
+# --------------------------------------------------------------------------
+# Comparison generator (include/mtgp_mt.h): host-only parameter code
+# --------------------------------------------------------------------------
+def test_mt_params_mt19937_matches_oracle(lib):
+    import oracle.mt as omt
+    assert mtgp.mtgp_mt_params_mt19937().as_dict() == omt.params_mt19937().as_dict()
+
+
+@pytest.mark.parametrize("p", [521, 3217, 4423, 19937, 44497])
+@pytest.mark.parametrize("seed", [0, 7, 0xC0FFEE])
+def test_mt_params_generate_matches_oracle(lib, p, seed):
+    import oracle.mt as omt
+    assert mtgp.mtgp_mt_params_generate(p, seed).as_dict() == omt.params_generate(p, seed).as_dict()
+
+
+def test_mt_params_generate_rejects_small_exponent(lib):
+    with pytest.raises(mtgp.MtgpError):
+        mtgp.mtgp_mt_params_generate(32, 1)
