@@ -68,24 +68,55 @@ __device__ __forceinline__ uint32_t mt_convert_rt(uint32_t z, uint32_t fmt)
     return fmt == 0 ? z : (fmt == 1 ? mt_convert<1>(z) : mt_convert<2>(z));
 }
 
-// A whole step inside one request: lane j of sub-step i takes number
-// k0 + 32 i + j.  bp = buf + off + lane, op = the lane's output for sub-step 0.
+// `nst` >= 1 whole steps inside one request, with room in the buffer for all
+// of them.  Lane j of sub-step i takes number k0 + 32 i + j of each step;
+// bp = buf + off + lane and op = the lane's output of the first step.  The
+// tempering, conversion and output store of step t run after the loads of
+// step t + 1 are issued, so they fill the load latency instead of lengthening
+// the chain from one step's state store to the next step's loads.
 template <int K, int FMT>
-__device__ __forceinline__ void mt_step_fast(const MtK& P, uint32_t* bp, uint32_t* op, bool lane_ok)
+__device__ __forceinline__ void mt_run_steps(const MtK& P, uint32_t* bp, uint32_t* op, uint32_t nst,
+                                             uint32_t lane)
 {
-    const uint32_t* bm = bp + P.m;
-    uint32_t* bn = bp + P.n;
+    const uint32_t W = P.W, m = P.m, n = P.n;
+    bool act[K];   // the lane takes part in sub-step i (W may end inside a sub-step)
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+        act[i] = 32u * i + lane < W;
     uint32_t xn[K];
 #pragma unroll
     for (int i = 0; i < K; ++i)
-        if (K > 1 || lane_ok)
-            xn[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bm[32 * i]);
+        if (act[i])
+            xn[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
 #pragma unroll
     for (int i = 0; i < K; ++i)
-        if (K > 1 || lane_ok) {
-            bn[32 * i] = xn[i];
+        if (act[i])
+            bp[32 * i + n] = xn[i];
+    __syncwarp();
+    for (uint32_t t = 1; t < nst; ++t) {
+        bp += W;
+        uint32_t xt[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if (act[i])
+                xt[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if (act[i])
+                __stcs(op + 32 * i, mt_convert<FMT>(mt_temper(P, xn[i])));
+        op += W;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if (act[i]) {
+                bp[32 * i + n] = xt[i];
+                xn[i] = xt[i];
+            }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+        if (act[i])
             __stcs(op + 32 * i, mt_convert<FMT>(mt_temper(P, xn[i])));
-        }
 }
 
 // A step that crosses a request boundary or the stream's end: each lane finds
@@ -119,7 +150,7 @@ __device__ __forceinline__ void mt_step_slow(const MtK& P, uint32_t* bp, uint64_
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) mt_gen_kernel(const MtK P, uint32_t* __restrict__ states,
+__global__ void __launch_bounds__(128) mt_gen_kernel(const MtK P, uint32_t* __restrict__ states,
                                                      uint32_t n_streams,
                                                      const WorkItem* __restrict__ items,
                                                      const Segment* __restrict__ segs,
@@ -130,7 +161,6 @@ __global__ void __launch_bounds__(256) mt_gen_kernel(const MtK P, uint32_t* __re
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t* buf = smem + (threadIdx.x >> 5) * P.B;
     const uint32_t N = P.n, W = P.W;
-    const bool lane_ok = lane < W;
 
     for (;;) {
         uint32_t it = 0;
@@ -156,12 +186,13 @@ __global__ void __launch_bounds__(256) mt_gen_kernel(const MtK P, uint32_t* __re
         uint32_t si = w.seg_begin;
         Segment sg = segs[si];
         uint64_t seg_hi = sg.g_start + sg.count;
-        uint64_t k0 = 0;    // first number of the step
+        uint64_t k0 = 0;    // first number of the next step
         uint32_t off = 0;   // buffer position of x_{k0}
         while (k0 < total) {
             if (off + N + W > P.B) {
                 // move the live window [off, off + n) to the start; off >= n
                 // here (B >= 2n + W), so source and destination are disjoint
+#pragma unroll 4
                 for (uint32_t j = lane; j < N; j += 32u)
                     buf[j] = buf[off + j];
                 __syncwarp();
@@ -173,19 +204,25 @@ __global__ void __launch_bounds__(256) mt_gen_kernel(const MtK P, uint32_t* __re
             }
             uint32_t* bp = buf + off + lane;
             if (k0 + W <= seg_hi) {
+                // whole steps of this request, as many as the buffer holds
+                const uint64_t n_seg = (seg_hi - k0) / W;
+                const uint32_t n_buf = (P.B - N - W - off) / W + 1u;
+                const uint32_t nst = n_seg < n_buf ? (uint32_t)n_seg : n_buf;
                 uint32_t* op = out + (sg.out_off - sg.g_start) + k0 + lane;
                 if (sg.fmt == 0)
-                    mt_step_fast<K, 0>(P, bp, op, lane_ok);
+                    mt_run_steps<K, 0>(P, bp, op, nst, lane);
                 else if (sg.fmt == 1)
-                    mt_step_fast<K, 1>(P, bp, op, lane_ok);
+                    mt_run_steps<K, 1>(P, bp, op, nst, lane);
                 else
-                    mt_step_fast<K, 2>(P, bp, op, lane_ok);
+                    mt_run_steps<K, 2>(P, bp, op, nst, lane);
+                k0 += (uint64_t)nst * W;
+                off += nst * W;
             } else {
                 mt_step_slow<K>(P, bp, k0, total, segs, si, s_end, out, lane);
+                __syncwarp();
+                k0 += W;
+                off += W;
             }
-            __syncwarp();
-            k0 += W;
-            off += W;
         }
         // the state after `total` numbers is x_total .. x_{total+n-1}
         const uint32_t first = off - (uint32_t)(k0 - total);
@@ -197,8 +234,16 @@ __global__ void __launch_bounds__(256) mt_gen_kernel(const MtK P, uint32_t* __re
 
 const void* mt_kernel_ptr(int K)
 {
-    return K == 4 ? (const void*)mt_gen_kernel<4>
-                  : (K == 2 ? (const void*)mt_gen_kernel<2> : (const void*)mt_gen_kernel<1>);
+    switch (K) {
+    case 8:
+        return (const void*)mt_gen_kernel<8>;
+    case 4:
+        return (const void*)mt_gen_kernel<4>;
+    case 2:
+        return (const void*)mt_gen_kernel<2>;
+    default:
+        return (const void*)mt_gen_kernel<1>;
+    }
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014): golden-ratio increment, then two
@@ -335,9 +380,13 @@ extern "C" mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t
         k.mul_t = 1u << p.t;
         k.b = p.b;
         k.c = p.c;
-        const uint32_t gap = p.n - p.m;
-        h->K = gap >= 128u ? 4 : (gap >= 64u ? 2 : 1);
-        k.W = h->K > 1 ? 32u * (uint32_t)h->K : std::min(32u, gap);
+        // a step takes W = n - m numbers (the recurrence's parallel width),
+        // at most 256: K = the smallest power of two with 32 K >= W
+        const uint32_t gap = std::min(p.n - p.m, 256u);
+        h->K = 1;
+        while (32u * (uint32_t)h->K < gap)
+            h->K *= 2;
+        k.W = gap;
         // about 16 n words (move overhead 2n per 14n numbers), capped at
         // 4096 words so that a dozen warps fit on an SM
         uint32_t B = std::max(2u * p.n + k.W, std::min(16u * p.n, 4096u));
@@ -474,19 +523,13 @@ extern "C" mtgp_status mtgp_mt_generate(mtgp_mt_t h, const uint32_t* ids, const 
         const Segment* segs = (const Segment*)((char*)sl.dev + so);
         uint32_t* counter = (uint32_t*)sl.dev;
         uint32_t* o = (uint32_t*)out;
-        switch (h->K) {
-        case 4:
-            mt_gen_kernel<4><<<grid, h->threads, h->smem, s>>>(h->k, h->d_states, h->n_streams, items,
-                                                             segs, n_items, counter, o, h->d_err);
-            break;
-        case 2:
-            mt_gen_kernel<2><<<grid, h->threads, h->smem, s>>>(h->k, h->d_states, h->n_streams, items,
-                                                             segs, n_items, counter, o, h->d_err);
-            break;
-        default:
-            mt_gen_kernel<1><<<grid, h->threads, h->smem, s>>>(h->k, h->d_states, h->n_streams, items,
-                                                             segs, n_items, counter, o, h->d_err);
-        }
+        MtK P = h->k;
+        uint32_t* states = h->d_states;
+        uint32_t n_streams = h->n_streams;
+        int* err = h->d_err;
+        void* args[] = {&P, &states, &n_streams, &items, &segs, (void*)&n_items, &counter, &o, &err};
+        MT_TRY(cudaLaunchKernel(mt_kernel_ptr(h->K), dim3(grid), dim3(h->threads), args, h->smem, s),
+               "MT generation kernel launch");
         MT_TRY(cudaGetLastError(), "MT generation kernel launch");
         MT_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
         sl.ev_recorded = true;
