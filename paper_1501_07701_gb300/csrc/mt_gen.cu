@@ -34,8 +34,10 @@ struct MtK {
     uint32_t u, l;           // right shifts of the tempering
     uint32_t mul_s, mul_t;   // 2^s, 2^t: the tempering's left shifts as multiplies
     uint32_t b, c;
-    uint32_t W;              // numbers per step: 32 K, or n - m when that is below 32 (K = 1)
-    uint32_t B;              // words of each warp's sliding buffer, >= 2 n + W
+    uint32_t W;              // numbers per step: min(n - m, 256) <= 32 K
+    uint32_t B;              // words of the sliding window's range, >= 2 n + W
+    uint32_t stride;         // words per warp: B plus 32 K words of slack that
+                             // lanes past W may read
 };
 
 __device__ __forceinline__ uint32_t mt_twist(const MtK& P, uint32_t xk, uint32_t xk1, uint32_t xm)
@@ -70,53 +72,58 @@ __device__ __forceinline__ uint32_t mt_convert_rt(uint32_t z, uint32_t fmt)
 
 // `nst` >= 1 whole steps inside one request, with room in the buffer for all
 // of them.  Lane j of sub-step i takes number k0 + 32 i + j of each step;
-// bp = buf + off + lane and op = the lane's output of the first step.  The
-// tempering, conversion and output store of step t run after the loads of
-// step t + 1 are issued, so they fill the load latency instead of lengthening
-// the chain from one step's state store to the next step's loads.
+// bp = buf + off + lane and op = the lane's output of the first step.
+// Lanes past W (32 K > W) load and compute too, on words of the buffer's
+// slack, so the step has no branches; only their two stores are predicated
+// off.  The tempering, conversion and output store of step t run after the
+// loads of step t + 1 are issued, so they fill the load latency instead of
+// lengthening the chain from one step's state store to the next step's loads.
 template <int K, int FMT>
 __device__ __forceinline__ void mt_run_steps(const MtK& P, uint32_t* bp, uint32_t* op, uint32_t nst,
                                              uint32_t lane)
 {
     const uint32_t W = P.W, m = P.m, n = P.n;
-    bool act[K];   // the lane takes part in sub-step i (W may end inside a sub-step)
+    bool act[K];   // the lane's number in sub-step i belongs to the step
 #pragma unroll
     for (int i = 0; i < K; ++i)
         act[i] = 32u * i + lane < W;
     uint32_t xn[K];
 #pragma unroll
     for (int i = 0; i < K; ++i)
-        if (act[i])
-            xn[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
+        xn[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
 #pragma unroll
     for (int i = 0; i < K; ++i)
         if (act[i])
             bp[32 * i + n] = xn[i];
     __syncwarp();
+#pragma unroll 2
     for (uint32_t t = 1; t < nst; ++t) {
         bp += W;
         uint32_t xt[K];
 #pragma unroll
         for (int i = 0; i < K; ++i)
-            if (act[i])
-                xt[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
+            xt[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
 #pragma unroll
-        for (int i = 0; i < K; ++i)
+        for (int i = 0; i < K; ++i) {
+            const uint32_t o = mt_convert<FMT>(mt_temper(P, xn[i]));
             if (act[i])
-                __stcs(op + 32 * i, mt_convert<FMT>(mt_temper(P, xn[i])));
+                __stcs(op + 32 * i, o);
+        }
         op += W;
 #pragma unroll
-        for (int i = 0; i < K; ++i)
-            if (act[i]) {
+        for (int i = 0; i < K; ++i) {
+            if (act[i])
                 bp[32 * i + n] = xt[i];
-                xn[i] = xt[i];
-            }
+            xn[i] = xt[i];
+        }
         __syncwarp();
     }
 #pragma unroll
-    for (int i = 0; i < K; ++i)
+    for (int i = 0; i < K; ++i) {
+        const uint32_t o = mt_convert<FMT>(mt_temper(P, xn[i]));
         if (act[i])
-            __stcs(op + 32 * i, mt_convert<FMT>(mt_temper(P, xn[i])));
+            __stcs(op + 32 * i, o);
+    }
 }
 
 // A step that crosses a request boundary or the stream's end: each lane finds
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(128) mt_gen_kernel(const MtK P, uint32_t* __re
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
-    uint32_t* buf = smem + (threadIdx.x >> 5) * P.B;
+    uint32_t* buf = smem + (threadIdx.x >> 5) * P.stride;
     const uint32_t N = P.n, W = P.W;
 
     for (;;) {
@@ -391,6 +398,8 @@ extern "C" mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t
         // 4096 words so that a dozen warps fit on an SM
         uint32_t B = std::max(2u * p.n + k.W, std::min(16u * p.n, 4096u));
         k.B = (B + 31u) & ~31u;
+        // a lane j < 32 K reads up to position off + 32 K - 1 + m < off + n + 32 K
+        k.stride = k.B + 32u * (uint32_t)h->K;
         auto bail = [&](cudaError_t e, const char* what) {
             mtgp_status s2 = fail_cuda(e, what);
             destroy_mt(h);
@@ -411,7 +420,7 @@ extern "C" mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t
         // launch geometry: kWarpsPerCta warps per CTA, as many CTAs as fit
         const void* fn = mt_kernel_ptr(h->K);
         h->threads = 32 * kWarpsPerCta;
-        h->smem = (size_t)kWarpsPerCta * k.B * 4u;
+        h->smem = (size_t)kWarpsPerCta * k.stride * 4u;
         if (h->smem > 48u * 1024u && (e = allow_max_dynamic_smem(fn, h->device, h->smem)) != cudaSuccess)
             return bail(e, "dynamic shared memory limit");
         int per_sm = 0, sms = 0;
