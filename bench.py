@@ -70,10 +70,11 @@ def recorded_traffic(kernel: str, workload_name: str):
 
 
 def workload(name: str, rank: int, streams: int = 0, count: int = 0, param_sets: int = 0,
-             generator: str = ""):
+             generator: str = "", mexp: int = 0):
     """Seeds and counts of a named workload; `generator` replaces the MTGP32
-    label in the description (the comparison generator runs the same shapes)."""
-    gen = generator or "MTGP32 Mexp 11213"
+    label in the description (the comparison generator runs the same shapes)
+    and `mexp` the workload's MTGP exponent."""
+    gen = generator or "MTGP32 Mexp %d" % (mexp or workloads.MEXP_MAIN)
     if name == "uneven":
         w = workloads.uneven()
         desc = "uneven: 10000 %s streams, counts floor(2^U), U~U[10,22] (seed 7)" % gen
@@ -91,6 +92,8 @@ def workload(name: str, rank: int, streams: int = 0, count: int = 0, param_sets:
         desc = "long: 1024 %s streams x 2^20" % (generator or "MTGP32 Mexp " + name[4:])
     else:
         raise SystemExit("unknown workload " + name)
+    if mexp:
+        w["mexp"] = mexp
     w["seeds"] = mdist.weak_seeds(w["seeds"], rank)
     w["param_seeds"] = None
     if param_sets:
@@ -212,7 +215,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    w, desc = workload(args.workload, 0, args.streams, args.count, args.param_sets)
+    w, desc = workload(args.workload, 0, args.streams, args.count, args.param_sets, mexp=args.mexp)
     # each step: a bounded sample sized so the whole run stays within ~2 minutes
     per_step = min(10.0, max(0.05, 100.0 / max(1, args.steps + args.warmup)))
     vals, secs, nums = [], [], []
@@ -249,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w, desc = workload(args.workload, rank, args.streams, args.count, args.param_sets)
+    w, desc = workload(args.workload, rank, args.streams, args.count, args.param_sets, mexp=args.mexp)
     counts = w["counts"]
     total = int(counts.sum())
     stream = torch.cuda.Stream()
@@ -610,6 +613,8 @@ def main():
     ap.add_argument("--no-quality", dest="quality", action="store_false",
                     help="skip the gap and Hamming-weight statistics over the generated output")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mexp", type=int, default=0,
+                    help="MTGP exponent of the workload (0 = the workload's own, 11213 for uneven)")
     ap.add_argument("--generator", default="mtgp", choices=["mtgp", "mt"],
                     help="mt: the original Mersenne Twister of Sec. 5.3 on the same workload")
     ap.add_argument("--mt-p", type=int, default=3217,

@@ -292,7 +292,8 @@ struct mtgp_mt {
     TableSlot slot{};
     int threads = 0;
     size_t smem = 0;
-    int grid_cap = 0;
+    int grid_cap = 0;   // resident CTAs on the device
+    int sms = 0;
 };
 
 static void destroy_mt(mtgp_mt* h)
@@ -433,6 +434,7 @@ extern "C" mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t
             cudaSuccess)
             return bail(e, "cudaDeviceGetAttribute");
         h->grid_cap = sms * per_sm;
+        h->sms = sms;
         // seeds -> states with the MT-family seeding kernel shared with MTGP
         KParams kp;
         std::memset(&kp, 0, sizeof kp);
@@ -525,8 +527,14 @@ extern "C" mtgp_status mtgp_mt_generate(mtgp_mt_t h, const uint32_t* ids, const 
         fill_table(w, sl.host);
         MT_TRY(cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, s),
                "cudaMemcpyAsync(work table)");
+        // Warp count: every stream runs on one warp, longest first, so the
+        // launch cannot end before its longest stream does.  About
+        // total / longest warps keep pace with that stream; more warps only
+        // slow it down by sharing its SM.  At least one CTA per SM.
         const uint32_t n_items = (uint32_t)w.items.size();
-        const long long want = ((long long)n_items + kWarpsPerCta - 1) / kWarpsPerCta;
+        const long long pace = (long long)((w.total + w.max_item - 1) / w.max_item);
+        const long long warps = std::max<long long>(pace, (long long)h->sms * kWarpsPerCta);
+        const long long want = (std::min<long long>(n_items, warps) + kWarpsPerCta - 1) / kWarpsPerCta;
         const int grid = (int)std::max(1LL, std::min<long long>(want, h->grid_cap));
         const WorkItem* items = (const WorkItem*)((char*)sl.dev + io);
         const Segment* segs = (const Segment*)((char*)sl.dev + so);
