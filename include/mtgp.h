@@ -212,7 +212,7 @@ typedef struct {
     uint32_t warps_per_cta;   /* block size / 32: 1..8 (the register-resident
                                  path uses 2, 4 or 8)                          */
     uint32_t ctas_per_sm;     /* resident CTAs per SM (0 = occupancy maximum)   */
-    uint32_t words_per_lane;  /* sub-steps per parallel step (4 or 8); the
+    uint32_t words_per_lane;  /* sub-steps per parallel step (2, 4 or 8); the
                                  window is 32 * words_per_lane <= N - pos      */
     uint32_t kernel;          /* 0 = register-resident path when available,
                                  1 = shared-memory ring path (any parameters)  */

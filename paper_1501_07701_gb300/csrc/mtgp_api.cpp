@@ -585,7 +585,8 @@ extern "C" mtgp_status mtgp_init_statuses_multi(const mtgp_params_t* sets, uint3
 LaunchCfg mtgp::default_config(const KParams& P)
 {
     // 8 warps per SM; 128-word software-pipelined steps when the parameter
-    // set allows them (N - pos >= 256), else 256-word steps, else 128.
+    // set allows them (N - pos >= 256), else 256-word steps, else 128, else
+    // 64 (short states such as Mexp 3217).
     LaunchCfg c;
     c.warps_per_cta = 4;
     c.ctas_per_sm = 2;
@@ -593,7 +594,7 @@ LaunchCfg mtgp::default_config(const KParams& P)
     c.kernel = 0;
     c.coop_percent = 0;
     if (P.n - P.pos < 256u || !fast_supported(P, 4))
-        c.k = fast_supported(P, 8) ? 8 : 4;
+        c.k = fast_supported(P, 8) ? 8 : (fast_supported(P, 4) || !fast_supported(P, 2) ? 4 : 2);
     return c;
 }
 
@@ -924,8 +925,8 @@ mtgp_status mtgp::validate_config(const mtgp_launch_config* c, LaunchCfg* out)
         return fail(MTGP_EINVAL, "null config");
     if (c->warps_per_cta < 1 || c->warps_per_cta > 8)
         return fail(MTGP_EINVAL, "warps_per_cta %u not in 1..8", c->warps_per_cta);
-    if (c->words_per_lane != 4 && c->words_per_lane != 8)
-        return fail(MTGP_EINVAL, "words_per_lane %u not 4 or 8", c->words_per_lane);
+    if (c->words_per_lane != 2 && c->words_per_lane != 4 && c->words_per_lane != 8)
+        return fail(MTGP_EINVAL, "words_per_lane %u not 2, 4 or 8", c->words_per_lane);
     if (c->kernel > 1)
         return fail(MTGP_EINVAL, "kernel %u not 0 or 1", c->kernel);
     if (c->ctas_per_sm > 64)
@@ -971,7 +972,7 @@ std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
         x.coop_percent = coop;
         v.push_back(x);
     };
-    for (int k : {8, 4}) {
+    for (int k : {8, 4, 2}) {
         for (int cap : {1, 2, 3, 4, 0})
             add(4, k, cap, 0);
         for (int cap : {2, 3, 4, 6, 0})

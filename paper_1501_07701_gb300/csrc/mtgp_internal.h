@@ -58,7 +58,7 @@ struct Segment {
 struct LaunchCfg {
     int warps_per_cta;   // G: 2, 4 or 8 for the register-resident kernel (1..8 ring)
     int ctas_per_sm;     // 0 = occupancy maximum
-    int k;               // sub-steps per parallel step (words per lane), 4 or 8
+    int k;               // sub-steps per parallel step (words per lane), 2, 4 or 8
     int kernel;          // 0 register-resident, 1 shared-memory ring
     int coop_percent;    // streams longer than coop_percent/100 x (numbers per warp
                          // slot) are advanced by a whole CTA; 0 = never

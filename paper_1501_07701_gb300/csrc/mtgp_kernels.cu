@@ -190,7 +190,7 @@ static int fast_m(const KParams& P) { return (int)((P.n + 31u) / 32u); }
 
 bool fast_supported(const KParams& P, int k, int g)
 {
-    if (k != 4 && k != 8)
+    if (k != 2 && k != 4 && k != 8)
         return false;
     if (P.n < 64 || 32u * (uint32_t)k > P.n - P.pos)
         return false;
@@ -214,6 +214,9 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
         if (!fast_supported(P, k, warps)) {
             if (fast_supported(P, 4, std::min(warps, 4))) {
                 k = 4;
+                warps = std::min(warps, 4);
+            } else if (fast_supported(P, 2, std::min(warps, 4))) {
+                k = 2;   // short states (Mexp 3217: N - pos < 128)
                 warps = std::min(warps, 4);
             } else {
                 kernel = 1;
@@ -278,6 +281,7 @@ namespace mtgp {
 const void* fast_ptr_group_a(int M, int K, int G);
 const void* fast_ptr_group_b(int M, int K, int G);
 const void* fast_ptr_group_c(int M, int K, int G);
+const void* fast_ptr_group_d(int M, int K, int G);
 
 const void* fast_kernel_ptr(int M, int K, int G)
 {
@@ -286,6 +290,8 @@ const void* fast_kernel_ptr(int M, int K, int G)
         p = fast_ptr_group_b(M, K, G);
     if (!p)
         p = fast_ptr_group_c(M, K, G);
+    if (!p)
+        p = fast_ptr_group_d(M, K, G);
     return p;
 }
 

@@ -200,6 +200,51 @@ def test_parameter_sweep(kernel, mexp, pseed):
     _assert_same(mtgp.mtgp_get_statuses(st), states)
 
 
+@pytest.mark.parametrize("mexp", [3217, 4253, 4423])
+@pytest.mark.parametrize("pseed", [workloads.PARAM_SEED, 1, 2])
+@pytest.mark.parametrize("warps,k,coop", [(4, 2, 0), (2, 2, 0), (8, 2, 0), (2, 2, 1), (4, 4, 0),
+                                          (2, 4, 1)])
+def test_short_states_register_kernel(mexp, pseed, warps, k, coop):
+    """Mexp 3217 (N = 101, the paper's exponent) and 4253 / 4423 (N = 133 /
+    139) on the register-resident kernel: 64-word steps (K = 2) for every
+    set, 128-word steps where N - pos >= 128, warp-owned and CTA-owned
+    streams.  The plan reports the kernel and step width it resolved to."""
+    gp, op = _both_params(mexp, pseed)
+    if 32 * k > op.n - op.pos:
+        pytest.skip("N - pos = %d admits no %d-word step" % (op.n - op.pos, 32 * k))
+    n = 10
+    st = mtgp.mtgp_init_statuses(gp, np.arange(n, dtype=np.uint32))
+    mtgp.mtgp_set_launch_config(st, warps_per_cta=warps, words_per_lane=k, kernel=0,
+                                coop_percent=coop)
+    states = np.stack([oracle.init_state(op, s) for s in range(n)])
+    ids = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 2, 2], np.uint32)
+    counts = np.array([op.n * 40 + 7, 1, 63, 64, 65, op.n, op.n - 1, 30000, 0, 2 * op.n + 1, 10,
+                       op.n * 3], np.uint64)
+    for fmt in FMTS:
+        out = _gpu_generate(st, ids, counts, fmt)
+        ref, states = oracle.generate_many(op, states, ids, counts, fmt, THREADS)
+        _assert_same(out, ref, "mexp %d seed %d fmt %d" % (mexp, pseed, fmt))
+    _assert_same(mtgp.mtgp_get_statuses(st), states)
+    out = torch.empty(int(counts.sum()), dtype=torch.int32, device="cuda")
+    plan = mtgp.mtgp_plan_create(st, ids, counts, mtgp.MTGP_U32, out)
+    info = mtgp.mtgp_plan_get_info(plan)
+    assert info["config"]["kernel"] == 0 and info["config"]["words_per_lane"] == k
+    mtgp.mtgp_plan_launch(plan)
+    torch.cuda.synchronize()
+    ref, states = oracle.generate_many(op, states, ids, counts, 0, THREADS)
+    _assert_same(out.cpu().numpy().view(np.uint32), ref, "plan")
+    _assert_same(mtgp.mtgp_get_statuses(st), states)
+
+
+def test_short_state_default_config_uses_register_kernel():
+    gp, op = _both_params(3217)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(4, dtype=np.uint32))
+    out = torch.empty(4000, dtype=torch.int32, device="cuda")
+    plan = mtgp.mtgp_plan_create(st, np.arange(4), np.full(4, 1000), mtgp.MTGP_U32, out)
+    info = mtgp.mtgp_plan_get_info(plan)
+    assert info["config"]["kernel"] == 0 and info["config"]["words_per_lane"] == 2
+
+
 @pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("mexp,n", [(23209, 727), (44497, 1392)])
 def test_literal_state_sizes(tmp_path, mexp, n, kernel):
