@@ -531,6 +531,77 @@ def run_mt(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_quality_sweep(args):
+    """Sec. 5.3 restated on this library: many parameter sets of MTGP and of
+    the original MT at the same period 2^p, one stream per set from seed
+    status 0 (Sec. 5.1), each stream's output put through the statistics of
+    tests 35 and 100 on the GPU; the line reports the fraction of sets whose
+    p-values stay inside [0.001, 0.999] (TestU01's suspect bounds).  The
+    sets are seed-generated, not made by the dynamic creators, and the
+    statistics are this library's restatement, not TestU01's."""
+    import torch
+    import oracle
+    import oracle.mt as omt
+    from paper_1501_07701_gb300 import mtgp, quality
+    from paper_1501_07701_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+    S, C, p = args.quality_sweep, args.sweep_count, args.mexp or 3217
+    bounds = quality.default_hamming_bounds(1200, 4)
+    counts = np.full(S, C, np.uint64)
+    ids = np.arange(S, dtype=np.uint32)
+    seeds = np.zeros(S, np.uint32)
+    out = torch.empty(S * C, dtype=torch.int32, device="cuda")
+    inside = lambda v: 1e-3 <= v <= 1.0 - 1e-3  # noqa: E731
+    res = {}
+    for gen in ("mtgp", "mt"):
+        if gen == "mtgp":
+            sets = [mtgp.mtgp_params_generate(p, k) for k in range(S)]
+            st = mtgp.mtgp_init_statuses_multi(sets, ids, seeds)
+        else:
+            sets = [mtgp.mtgp_mt_params_generate(p, k) for k in range(S)]
+            st = mtgp.mtgp_mt_init_multi(sets, ids, seeds)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        if gen == "mtgp":
+            mtgp.mtgp_generate_u32(st, ids, counts, out)
+        else:
+            mtgp.mtgp_mt_generate(st, ids, counts, mtgp.MTGP_U32, out)
+        e1.record()
+        hist = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128)
+        tab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds)
+        e2.record()
+        torch.cuda.synchronize()
+        # bit-exact check of the first 2^16 outputs of three sets against the oracles
+        exact = True
+        for k in sorted({0, S // 2, S - 1}):
+            if gen == "mtgp":
+                q = oracle.params_generate(p, k)
+                ref, _ = oracle.generate(q, oracle.init_state(q, 0), min(C, 1 << 16))
+            else:
+                q = omt.params_generate(p, k)
+                ref, _ = omt.generate(q, omt.init_state(q, 0), min(C, 1 << 16))
+            got = out[k * C:k * C + ref.size].cpu().numpy().view(np.uint32)
+            exact = exact and bool(np.array_equal(got, ref))
+        pg = np.array([quality.gap_test(hist[i], b=5)["p_value"] for i in range(S)])
+        ph = np.array([quality.hamming_test(tab[i], L=1200, bounds=bounds)["p_value"]
+                       for i in range(S)])
+        ok_g = np.array([inside(v) for v in pg])
+        ok_h = np.array([inside(v) for v in ph])
+        res[gen] = {"sets": S, "pass_gap": float(ok_g.mean()), "pass_hamming": float(ok_h.mean()),
+                    "pass_both": float((ok_g & ok_h).mean()),
+                    "gap_p_below_1e-3": int((pg < 1e-3).sum()),
+                    "hamming_p_below_1e-3": int((ph < 1e-3).sum()),
+                    "gen_gnum_s": S * C / (e0.elapsed_time(e1) * 1e6),
+                    "stats_ms": e1.elapsed_time(e2), "bit_exact_sample": exact}
+        del st
+    print(json.dumps({"quality_sweep": {"period_exponent": p, "numbers_per_set": C,
+                                        "seed_status": 0, "tests": "gap r=25 b=5 t=128; "
+                                        "Hamming pairs r=25 s=5 L=1200, 4 classes",
+                                        "suspect_bounds": [1e-3, 1 - 1e-3], **res}}), flush=True)
+
+
 def spot_check(w, counts, out, states0, fmt):
     """Whole outputs of a few streams of the first launch vs the oracle."""
     import oracle
@@ -617,6 +688,10 @@ def main():
                     help="MTGP exponent of the workload (0 = the workload's own, 11213 for uneven)")
     ap.add_argument("--generator", default="mtgp", choices=["mtgp", "mt"],
                     help="mt: the original Mersenne Twister of Sec. 5.3 on the same workload")
+    ap.add_argument("--quality-sweep", type=int, default=0,
+                    help="S > 0: tests 35 and 100 over S parameter sets of MTGP and of the original "
+                         "MT at period 2^mexp (default 3217), one stream each (Sec. 5.3)")
+    ap.add_argument("--sweep-count", type=int, default=1 << 24, help="numbers per set in the sweep")
     ap.add_argument("--mt-p", type=int, default=3217,
                     help="exponent of the original-MT set (19937 = MT19937, else seed-generated)")
     args = ap.parse_args()
@@ -629,6 +704,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.quality_sweep:
+        run_quality_sweep(args)
     elif args.generator == "mt":
         run_mt(args, rank, world, local_rank)
     else:

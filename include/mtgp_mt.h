@@ -68,6 +68,16 @@ mtgp_status mtgp_mt_params_generate(uint32_t p, uint64_t seed, mtgp_mt_params* o
 mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t* seeds, uint32_t n_streams,
                          void* cuda_stream, mtgp_mt_t* out);
 
+/* One parameter set per stream (the paper's setting: one parameterized
+ * status per generator, Sec. 4.1 and 5.3): stream s uses
+ * sets[set_of_stream[s]] (host arrays; the sets are copied).  All sets must
+ * share p, n and r; m, a and the tempering may differ.  MTGP_EINVAL if a set
+ * is invalid, the sets disagree on the state size, or an index is >= n_sets.
+ * Seeding and everything else as mtgp_mt_init. */
+mtgp_status mtgp_mt_init_multi(const mtgp_mt_params* sets, uint32_t n_sets,
+                               const uint32_t* set_of_stream, const uint32_t* seeds,
+                               uint32_t n_streams, void* cuda_stream, mtgp_mt_t* out);
+
 /* Host <-> device copies of all states (n_streams x n words, oldest word
  * first).  Both synchronise cuda_stream. */
 mtgp_status mtgp_mt_set_statuses(mtgp_mt_t mt, const uint32_t* states, void* cuda_stream);

@@ -1,6 +1,6 @@
 // The original Mersenne Twister (Matsumoto and Nishimura 1998), the
 // comparison generator of Sec. 5.3, for many independently seeded streams of
-// one parameter set on sm_103a.
+// one parameter set, or of one set per stream, on sm_103a.
 //
 // One warp advances one stream.  The stream's words live in a per-warp
 // sliding buffer in shared memory: x_k sits at buf[off + (k - k0)] while the
@@ -26,32 +26,42 @@ using namespace mtgp;
 
 namespace {
 
-// Kernel form of a parameter set (by value, in the kernel-parameter bank).
-struct MtK {
-    uint32_t n, np, m;
-    uint32_t upper;          // the top 32 - r bits
+// The fields in which the parameter sets of one handle may differ (they all
+// share p, n and r).
+struct MtSet {
+    uint32_t m;
     uint32_t a;
     uint32_t u, l;           // right shifts of the tempering
     uint32_t mul_s, mul_t;   // 2^s, 2^t: the tempering's left shifts as multiplies
     uint32_t b, c;
     uint32_t W;              // numbers per step: min(n - m, 256) <= 32 K
-    uint32_t B;              // words of the sliding window's range, >= 2 n + W
-    uint32_t stride;         // words per warp: B plus 32 K words of slack that
-                             // lanes past W may read
+    uint32_t pad[3];
 };
 
-__device__ __forceinline__ uint32_t mt_twist(const MtK& P, uint32_t xk, uint32_t xk1, uint32_t xm)
+// Kernel form of a handle (by value, in the kernel-parameter bank).
+struct MtK {
+    uint32_t n, np;
+    uint32_t upper;          // the top 32 - r bits
+    uint32_t B;              // words of the sliding window's range, >= 2 n + (largest W)
+    uint32_t stride;         // words per warp: B plus 32 K words of slack that
+                             // lanes past W may read
+    uint32_t pad[3];
+    MtSet set;               // the handle's set (streams without a set of their own)
+};
+
+__device__ __forceinline__ uint32_t mt_twist(uint32_t upper, const MtSet& S, uint32_t xk,
+                                             uint32_t xk1, uint32_t xm)
 {
-    const uint32_t y = (xk & P.upper) | (xk1 & ~P.upper);
-    return xm ^ (y >> 1) ^ ((y & 1u) * P.a);
+    const uint32_t y = (xk & upper) | (xk1 & ~upper);
+    return xm ^ (y >> 1) ^ ((y & 1u) * S.a);
 }
 
-__device__ __forceinline__ uint32_t mt_temper(const MtK& P, uint32_t x)
+__device__ __forceinline__ uint32_t mt_temper(const MtSet& S, uint32_t x)
 {
-    uint32_t z = x ^ (x >> P.u);
-    z ^= (z * P.mul_s) & P.b;
-    z ^= (z * P.mul_t) & P.c;
-    return z ^ (z >> P.l);
+    uint32_t z = x ^ (x >> S.u);
+    z ^= (z * S.mul_s) & S.b;
+    z ^= (z * S.mul_t) & S.c;
+    return z ^ (z >> S.l);
 }
 
 template <int FMT>
@@ -79,10 +89,10 @@ __device__ __forceinline__ uint32_t mt_convert_rt(uint32_t z, uint32_t fmt)
 // loads of step t + 1 are issued, so they fill the load latency instead of
 // lengthening the chain from one step's state store to the next step's loads.
 template <int K, int FMT>
-__device__ __forceinline__ void mt_run_steps(const MtK& P, uint32_t* bp, uint32_t* op, uint32_t nst,
-                                             uint32_t lane)
+__device__ __forceinline__ void mt_run_steps(const MtK& P, const MtSet& S, uint32_t* bp, uint32_t* op,
+                                             uint32_t nst, uint32_t lane)
 {
-    const uint32_t W = P.W, m = P.m, n = P.n;
+    const uint32_t W = S.W, m = S.m, n = P.n, upper = P.upper;
     bool act[K];   // the lane's number in sub-step i belongs to the step
 #pragma unroll
     for (int i = 0; i < K; ++i)
@@ -90,7 +100,7 @@ __device__ __forceinline__ void mt_run_steps(const MtK& P, uint32_t* bp, uint32_
     uint32_t xn[K];
 #pragma unroll
     for (int i = 0; i < K; ++i)
-        xn[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
+        xn[i] = mt_twist(upper, S, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
 #pragma unroll
     for (int i = 0; i < K; ++i)
         if (act[i])
@@ -102,10 +112,10 @@ __device__ __forceinline__ void mt_run_steps(const MtK& P, uint32_t* bp, uint32_
         uint32_t xt[K];
 #pragma unroll
         for (int i = 0; i < K; ++i)
-            xt[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
+            xt[i] = mt_twist(upper, S, bp[32 * i], bp[32 * i + 1], bp[32 * i + m]);
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            const uint32_t o = mt_convert<FMT>(mt_temper(P, xn[i]));
+            const uint32_t o = mt_convert<FMT>(mt_temper(S, xn[i]));
             if (act[i])
                 __stcs(op + 32 * i, o);
         }
@@ -120,7 +130,7 @@ __device__ __forceinline__ void mt_run_steps(const MtK& P, uint32_t* bp, uint32_
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        const uint32_t o = mt_convert<FMT>(mt_temper(P, xn[i]));
+        const uint32_t o = mt_convert<FMT>(mt_temper(S, xn[i]));
         if (act[i])
             __stcs(op + 32 * i, o);
     }
@@ -129,7 +139,8 @@ __device__ __forceinline__ void mt_run_steps(const MtK& P, uint32_t* bp, uint32_
 // A step that crosses a request boundary or the stream's end: each lane finds
 // the request of its own number.
 template <int K>
-__device__ __forceinline__ void mt_step_slow(const MtK& P, uint32_t* bp, uint64_t k0, uint64_t total,
+__device__ __forceinline__ void mt_step_slow(const MtK& P, const MtSet& S, uint32_t* bp, uint64_t k0,
+                                             uint64_t total,
                                              const Segment* __restrict__ segs, uint32_t si,
                                              uint32_t s_end, uint32_t* __restrict__ out,
                                              uint32_t lane)
@@ -138,20 +149,20 @@ __device__ __forceinline__ void mt_step_slow(const MtK& P, uint32_t* bp, uint64_
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const uint32_t j = 32u * i + lane;
-        if (j < P.W && k0 + j < total)
-            xn[i] = mt_twist(P, bp[32 * i], bp[32 * i + 1], bp[32 * i + P.m]);
+        if (j < S.W && k0 + j < total)
+            xn[i] = mt_twist(P.upper, S, bp[32 * i], bp[32 * i + 1], bp[32 * i + S.m]);
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const uint32_t j = 32u * i + lane;
         const uint64_t k = k0 + j;
-        if (j < P.W && k < total) {
+        if (j < S.W && k < total) {
             bp[32 * i + P.n] = xn[i];
             uint32_t s = si;
             while (s + 1u < s_end && k >= segs[s + 1u].g_start)
                 ++s;
             const Segment sg = segs[s];
-            out[sg.out_off + (k - sg.g_start)] = mt_convert_rt(mt_temper(P, xn[i]), sg.fmt);
+            out[sg.out_off + (k - sg.g_start)] = mt_convert_rt(mt_temper(S, xn[i]), sg.fmt);
         }
     }
 }
@@ -162,12 +173,14 @@ __global__ void __launch_bounds__(128) mt_gen_kernel(const MtK P, uint32_t* __re
                                                      const WorkItem* __restrict__ items,
                                                      const Segment* __restrict__ segs,
                                                      uint32_t n_items, uint32_t* __restrict__ counter,
-                                                     uint32_t* __restrict__ out, int* __restrict__ err)
+                                                     uint32_t* __restrict__ out, int* __restrict__ err,
+                                                     const MtSet* __restrict__ sets,
+                                                     const uint32_t* __restrict__ set_of)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t* buf = smem + (threadIdx.x >> 5) * P.stride;
-    const uint32_t N = P.n, W = P.W;
+    const uint32_t N = P.n;
 
     for (;;) {
         uint32_t it = 0;
@@ -182,6 +195,9 @@ __global__ void __launch_bounds__(128) mt_gen_kernel(const MtK P, uint32_t* __re
                 atomicOr(err, 1);
             continue;
         }
+        // the stream's own parameter set, or the handle's
+        const MtSet S = sets ? sets[set_of[w.stream]] : P.set;
+        const uint32_t W = S.W;
         uint32_t* g = states + (size_t)w.stream * P.np;
         for (uint32_t j = lane; j < N; j += 32u)
             buf[j] = g[j];
@@ -217,15 +233,15 @@ __global__ void __launch_bounds__(128) mt_gen_kernel(const MtK P, uint32_t* __re
                 const uint32_t nst = n_seg < n_buf ? (uint32_t)n_seg : n_buf;
                 uint32_t* op = out + (sg.out_off - sg.g_start) + k0 + lane;
                 if (sg.fmt == 0)
-                    mt_run_steps<K, 0>(P, bp, op, nst, lane);
+                    mt_run_steps<K, 0>(P, S, bp, op, nst, lane);
                 else if (sg.fmt == 1)
-                    mt_run_steps<K, 1>(P, bp, op, nst, lane);
+                    mt_run_steps<K, 1>(P, S, bp, op, nst, lane);
                 else
-                    mt_run_steps<K, 2>(P, bp, op, nst, lane);
+                    mt_run_steps<K, 2>(P, S, bp, op, nst, lane);
                 k0 += (uint64_t)nst * W;
                 off += nst * W;
             } else {
-                mt_step_slow<K>(P, bp, k0, total, segs, si, s_end, out, lane);
+                mt_step_slow<K>(P, S, bp, k0, total, segs, si, s_end, out, lane);
                 __syncwarp();
                 k0 += W;
                 off += W;
@@ -279,6 +295,23 @@ mtgp_status check_params(const mtgp_mt_params& p)
     return MTGP_OK;
 }
 
+MtSet make_set(const mtgp_mt_params& p)
+{
+    MtSet q;
+    std::memset(&q, 0, sizeof q);
+    q.m = p.m;
+    q.a = p.a;
+    q.u = p.u;
+    q.l = p.l;
+    q.mul_s = 1u << p.s;
+    q.mul_t = 1u << p.t;
+    q.b = p.b;
+    q.c = p.c;
+    // a step takes W = n - m numbers (the recurrence's parallel width), at most 256
+    q.W = std::min(p.n - p.m, 256u);
+    return q;
+}
+
 }  // namespace
 
 struct mtgp_mt {
@@ -294,6 +327,9 @@ struct mtgp_mt {
     size_t smem = 0;
     int grid_cap = 0;   // resident CTAs on the device
     int sms = 0;
+    // one parameter set per stream (mtgp_mt_init_multi); null: all use k.set
+    MtSet* d_sets = nullptr;
+    uint32_t* d_set_of = nullptr;
 };
 
 static void destroy_mt(mtgp_mt* h)
@@ -308,6 +344,10 @@ static void destroy_mt(mtgp_mt* h)
         cudaFree(h->d_states);
     if (h->d_err)
         cudaFree(h->d_err);
+    if (h->d_sets)
+        cudaFree(h->d_sets);
+    if (h->d_set_of)
+        cudaFree(h->d_set_of);
     delete h;
 }
 
@@ -361,43 +401,48 @@ extern "C" mtgp_status mtgp_mt_params_generate(uint32_t p, uint64_t seed, mtgp_m
     return ok();
 }
 
-extern "C" mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t* seeds,
-                                    uint32_t n_streams, void* cuda_stream, mtgp_mt_t* out)
+// Handle creation for one set (set_of null) or one set per stream.
+static mtgp_status init_handle(const mtgp_mt_params* sets, uint32_t n_sets, const uint32_t* set_of,
+                               const uint32_t* seeds, uint32_t n_streams, void* cuda_stream,
+                               mtgp_mt_t* out)
 {
     try {
-        if (!params || !out || !seeds)
+        if (!sets || !out || !seeds || n_sets == 0)
             return fail(MTGP_EINVAL, "null argument");
         if (n_streams == 0)
             return fail(MTGP_EINVAL, "n_streams must be >= 1");
-        mtgp_status st = check_params(*params);
-        if (st != MTGP_OK)
-            return st;
+        for (uint32_t i = 0; i < n_sets; ++i) {
+            mtgp_status st = check_params(sets[i]);
+            if (st != MTGP_OK)
+                return st;
+            if (sets[i].p != sets[0].p || sets[i].n != sets[0].n || sets[i].r != sets[0].r)
+                return fail(MTGP_EINVAL, "set %u: all sets of a handle need the same p, n and r", i);
+        }
+        uint32_t w_max = 0;
+        for (uint32_t i = 0; i < n_sets; ++i)
+            w_max = std::max(w_max, make_set(sets[i]).W);
+        if (set_of)
+            for (uint32_t s = 0; s < n_streams; ++s)
+                if (set_of[s] >= n_sets)
+                    return fail(MTGP_EINVAL, "stream %u: set index %u >= n_sets %u", s, set_of[s], n_sets);
+        const mtgp_mt_params* params = sets;
         mtgp_mt* h = new mtgp_mt;
         h->p = *params;
         h->n_streams = n_streams;
         const mtgp_mt_params& p = h->p;
         MtK& k = h->k;
+        std::memset(&k, 0, sizeof k);
         k.n = p.n;
         k.np = (p.n + 3u) & ~3u;
-        k.m = p.m;
         k.upper = 0xFFFFFFFFu << p.r;
-        k.a = p.a;
-        k.u = p.u;
-        k.l = p.l;
-        k.mul_s = 1u << p.s;
-        k.mul_t = 1u << p.t;
-        k.b = p.b;
-        k.c = p.c;
-        // a step takes W = n - m numbers (the recurrence's parallel width),
-        // at most 256: K = the smallest power of two with 32 K >= W
-        const uint32_t gap = std::min(p.n - p.m, 256u);
+        k.set = make_set(p);
+        // K = the smallest power of two with 32 K >= the widest step
         h->K = 1;
-        while (32u * (uint32_t)h->K < gap)
+        while (32u * (uint32_t)h->K < w_max)
             h->K *= 2;
-        k.W = gap;
         // about 16 n words (move overhead 2n per 14n numbers), capped at
         // 4096 words so that a dozen warps fit on an SM
-        uint32_t B = std::max(2u * p.n + k.W, std::min(16u * p.n, 4096u));
+        uint32_t B = std::max(2u * p.n + w_max, std::min(16u * p.n, 4096u));
         k.B = (B + 31u) & ~31u;
         // a lane j < 32 K reads up to position off + 32 K - 1 + m < off + n + 32 K
         k.stride = k.B + 32u * (uint32_t)h->K;
@@ -452,11 +497,40 @@ extern "C" mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t
         cudaFreeAsync(d_seeds, s);
         if (e != cudaSuccess)
             return bail(e, "init kernel launch");
+        if (set_of) {
+            std::vector<MtSet> ks(n_sets);
+            for (uint32_t i = 0; i < n_sets; ++i)
+                ks[i] = make_set(sets[i]);
+            if ((e = cudaMalloc(&h->d_sets, n_sets * sizeof(MtSet))) != cudaSuccess ||
+                (e = cudaMalloc(&h->d_set_of, (size_t)n_streams * 4)) != cudaSuccess)
+                return bail(e, "cudaMalloc(parameter sets)");
+            // pageable sources: both copies are complete when they return
+            if ((e = cudaMemcpyAsync(h->d_sets, ks.data(), n_sets * sizeof(MtSet), cudaMemcpyHostToDevice,
+                                     s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(h->d_set_of, set_of, (size_t)n_streams * 4, cudaMemcpyHostToDevice,
+                                     s)) != cudaSuccess)
+                return bail(e, "cudaMemcpyAsync(parameter sets)");
+        }
         *out = h;
         return ok();
     } catch (const std::bad_alloc&) {
         return fail(MTGP_ENOMEM, "host allocation failed");
     }
+}
+
+extern "C" mtgp_status mtgp_mt_init(const mtgp_mt_params* params, const uint32_t* seeds,
+                                    uint32_t n_streams, void* cuda_stream, mtgp_mt_t* out)
+{
+    return init_handle(params, 1, nullptr, seeds, n_streams, cuda_stream, out);
+}
+
+extern "C" mtgp_status mtgp_mt_init_multi(const mtgp_mt_params* sets, uint32_t n_sets,
+                                          const uint32_t* set_of_stream, const uint32_t* seeds,
+                                          uint32_t n_streams, void* cuda_stream, mtgp_mt_t* out)
+{
+    if (!set_of_stream)
+        return fail(MTGP_EINVAL, "null argument");
+    return init_handle(sets, n_sets, set_of_stream, seeds, n_streams, cuda_stream, out);
 }
 
 extern "C" mtgp_status mtgp_mt_set_statuses(mtgp_mt_t h, const uint32_t* states, void* cuda_stream)
@@ -544,7 +618,10 @@ extern "C" mtgp_status mtgp_mt_generate(mtgp_mt_t h, const uint32_t* ids, const 
         uint32_t* states = h->d_states;
         uint32_t n_streams = h->n_streams;
         int* err = h->d_err;
-        void* args[] = {&P, &states, &n_streams, &items, &segs, (void*)&n_items, &counter, &o, &err};
+        const MtSet* sets = h->d_sets;
+        const uint32_t* set_of = h->d_set_of;
+        void* args[] = {&P,       &states, &n_streams, &items, &segs, (void*)&n_items,
+                        &counter, &o,      &err,       &sets,  &set_of};
         MT_TRY(cudaLaunchKernel(mt_kernel_ptr(h->K), dim3(grid), dim3(h->threads), args, h->smem, s),
                "MT generation kernel launch");
         MT_TRY(cudaGetLastError(), "MT generation kernel launch");

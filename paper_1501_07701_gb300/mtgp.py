@@ -135,6 +135,8 @@ _SIGS = {
     "mtgp_mt_params_mt19937": [ctypes.POINTER(MtParams)],
     "mtgp_mt_params_generate": [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(MtParams)],
     "mtgp_mt_init": [ctypes.POINTER(MtParams), _U32P, ctypes.c_uint32, _VP, ctypes.POINTER(_VP)],
+    "mtgp_mt_init_multi": [ctypes.POINTER(MtParams), ctypes.c_uint32, _U32P, _U32P, ctypes.c_uint32,
+                           _VP, ctypes.POINTER(_VP)],
     "mtgp_mt_set_statuses": [_VP, _U32P, _VP],
     "mtgp_mt_get_statuses": [_VP, _U32P, _VP],
     "mtgp_mt_generate": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP, _VP],
@@ -627,6 +629,20 @@ def mtgp_mt_init(params: MtParams, seeds, stream=None) -> MtStreams:
     _call("mtgp_mt_init", ctypes.byref(q), _p32(seeds), seeds.size, _stream_handle(stream),
           ctypes.byref(h))
     return MtStreams(h, q, seeds.size)
+
+
+def mtgp_mt_init_multi(params_list, set_of_stream, seeds, stream=None) -> MtStreams:
+    """One parameter set per stream: stream s uses params_list[set_of_stream[s]]."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+    set_of = np.ascontiguousarray(set_of_stream, dtype=np.uint32)
+    if set_of.shape != seeds.shape:
+        raise ValueError("set_of_stream and seeds must have the same length")
+    arr = (MtParams * len(params_list))(
+        *[MtParams(*[getattr(q, f) for f, _ in MtParams._fields_]) for q in params_list])
+    h = _VP()
+    _call("mtgp_mt_init_multi", arr, len(params_list), _p32(set_of), _p32(seeds), seeds.size,
+          _stream_handle(stream), ctypes.byref(h))
+    return MtStreams(h, arr[0], seeds.size)
 
 
 def mtgp_mt_set_statuses(mt: MtStreams, states, stream=None):

@@ -159,3 +159,67 @@ def test_argument_errors_change_nothing():
     # an empty call is fine and launches nothing
     mtgp.mtgp_mt_generate(mt, [1, 2], [0, 0], mtgp.MTGP_U32, None)
     mtgp.mtgp_mt_check(mt)
+
+
+def _oracle_multi(osets, set_of, seeds, ids, counts, fmt):
+    """Per-stream sets on the oracle: requests in array order, each stream
+    with its own set."""
+    states = [omt.init_state(osets[set_of[s]], int(seeds[s])) for s in range(len(seeds))]
+    pieces = []
+    for i, c in zip(ids, counts):
+        o, states[i] = omt.generate(osets[set_of[i]], states[i], int(c), fmt)
+        pieces.append(o)
+    return np.concatenate(pieces) if pieces else np.zeros(0, np.uint32), np.stack(states)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+def test_one_set_per_stream(fmt):
+    """Seven seed-generated p = 3217 sets (a, b, c differ); stream s uses set
+    s mod 7."""
+    osets = [omt.params_generate(3217, 500 + k) for k in range(7)]
+    msets = [mtgp.mtgp_mt_params_generate(3217, 500 + k) for k in range(7)]
+    n = 40
+    seeds = np.arange(1000, 1000 + n, dtype=np.uint32)
+    set_of = (np.arange(n) % 7).astype(np.uint32)
+    mt = mtgp.mtgp_mt_init_multi(msets, set_of, seeds)
+    ids = np.concatenate([np.arange(n), [3, 3, 10]]).astype(np.uint32)
+    counts = np.array([(i * 7919) % 30011 for i in range(n)] + [1, 64, 5000], np.uint64)
+    out = torch.empty(int(counts.sum()), dtype=torch.int32, device="cuda")
+    mtgp.mtgp_mt_generate(mt, ids, counts, fmt, out)
+    ref, ref_states = _oracle_multi(osets, set_of, seeds, ids, counts, fmt)
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), ref)
+    np.testing.assert_array_equal(mtgp.mtgp_mt_get_statuses(mt), ref_states)
+
+
+def test_sets_with_different_step_widths():
+    """Sets of one state size whose m differ (W = n - m = 51, 71, 11 and 96):
+    the launch is shaped for the widest step and each stream steps at its
+    own width."""
+    base = omt.params_generate(3217, 9).as_dict()
+    osets = []
+    for m, a in [(50, 0x9908B0DF), (30, 0xB5026F5A), (90, 0x8E3A1C27), (5, 0xF00DF00D)]:
+        f = dict(base, m=m, a=a)
+        osets.append(omt.params_from_fields(**f))
+    msets = [mtgp.MtParams(*[getattr(q, f) for f, _ in mtgp.MtParams._fields_]) for q in osets]
+    n = 16
+    seeds = np.arange(n, dtype=np.uint32)
+    set_of = (np.arange(n) % 4).astype(np.uint32)
+    mt = mtgp.mtgp_mt_init_multi(msets, set_of, seeds)
+    ids = np.arange(n, dtype=np.uint32)
+    counts = np.array([0, 1, 11, 12, 51, 52, 71, 72, 96, 97, 1000, 3333, 20000, 65537, 5, 100000],
+                      np.uint64)
+    out = torch.empty(int(counts.sum()), dtype=torch.int32, device="cuda")
+    mtgp.mtgp_mt_generate(mt, ids, counts, mtgp.MTGP_U32, out)
+    ref, ref_states = _oracle_multi(osets, set_of, seeds, ids, counts, omt.U32)
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), ref)
+    np.testing.assert_array_equal(mtgp.mtgp_mt_get_statuses(mt), ref_states)
+
+
+def test_multi_set_argument_errors():
+    a = mtgp.mtgp_mt_params_generate(3217, 1)
+    b = mtgp.mtgp_mt_params_generate(4423, 1)
+    seeds = np.arange(4, dtype=np.uint32)
+    with pytest.raises(mtgp.MtgpError):
+        mtgp.mtgp_mt_init_multi([a, b], [0, 1, 0, 1], seeds)          # state sizes differ
+    with pytest.raises(mtgp.MtgpError):
+        mtgp.mtgp_mt_init_multi([a, a], [0, 1, 2, 0], seeds)          # index >= n_sets
