@@ -97,6 +97,20 @@ mtgp_status mtgp_mt_check(mtgp_mt_t mt, void* cuda_stream);
 
 mtgp_status mtgp_mt_free(mtgp_mt_t mt);
 
+/* The polynomial mu of a set's window transition (F mu(F) = 0, found as for
+ * mtgp_params_minpoly) and the period check of mtgp_params_period_check
+ * applied to it: *irreducible = 1 iff mu has degree p and is irreducible,
+ * i.e. for a Mersenne-prime p every nonzero state has period 2^p - 1
+ * (Sec. 5.3 compares MT and MTGP at equal period).  minpoly: *degree
+ * receives deg mu; words (may be null) receives its coefficients, bit i of
+ * words[i / 64] = coefficient of t^i (cap_words >= degree / 64 + 1).  Host
+ * computation, cached per set; the period check runs p squarings on the
+ * device (current device, cuda_stream) and synchronises it. */
+mtgp_status mtgp_mt_params_minpoly(const mtgp_mt_params* params, uint64_t* words, uint32_t cap_words,
+                                   int32_t* degree);
+mtgp_status mtgp_mt_params_period_check(const mtgp_mt_params* params, void* cuda_stream,
+                                        int32_t* irreducible);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@
 #include <random>
 #include <vector>
 
+#include "../../include/mtgp_mt.h"
 #include "mtgp_runtime.h"
 
 using namespace mtgp;
@@ -220,14 +221,43 @@ Poly berlekamp_massey(const std::vector<uint8_t>& s)
     return mu;
 }
 
+// The original Mersenne Twister's recursion on the host (words only):
+// x_{k+n} = x_{k+m} ^ (y >> 1) ^ (y odd ? a : 0), y = (x_k & upper) | (x_{k+1} & ~upper).
+struct MtRec {
+    uint32_t n, m, upper, a;
+};
+
+void host_sequence(const MtRec& p, const uint32_t* state, size_t count, std::vector<uint32_t>& seq)
+{
+    seq.assign(state, state + p.n);
+    seq.resize(p.n + count);
+    for (size_t k = 0; k < count; ++k) {
+        const uint32_t y = (seq[k] & p.upper) | (seq[k + 1] & ~p.upper);
+        seq[k + p.n] = seq[k + p.m] ^ (y >> 1) ^ ((y & 1u) ? p.a : 0u);
+    }
+}
+
+// Window size and the used bits of the window's oldest word.
+uint32_t window_words(const SetP& p) { return p.n; }
+uint32_t oldest_mask(const SetP& p) { return p.mask; }
+uint64_t rng_seed(const SetP& p)
+{
+    return 0x9E3779B97F4A7C15ull ^ ((uint64_t)p.pos << 32) ^ p.sh1 ^ ((uint64_t)p.rec[1] << 7);
+}
+uint32_t window_words(const MtRec& p) { return p.n; }
+uint32_t oldest_mask(const MtRec& p) { return p.upper; }
+uint64_t rng_seed(const MtRec& p) { return 0xC2B2AE3D27D4EB4Full ^ ((uint64_t)p.m << 32) ^ p.a; }
+
 // True if F mu(F) w = 0 for the sequence of `state`: for j = 1..N the XOR of
 // x_{k+j} over the set bits k of mu is zero.
-bool annihilates(const SetP& p, const Poly& mu, const uint32_t* state)
+template <class Rec>
+bool annihilates(const Rec& p, const Poly& mu, const uint32_t* state)
 {
     const int d = degree(mu);
     std::vector<uint32_t> seq;
-    host_sequence(p, state, (size_t)d + p.n + 1, seq);
-    for (uint32_t j = 1; j <= p.n; ++j) {
+    const uint32_t N = window_words(p);
+    host_sequence(p, state, (size_t)d + N + 1, seq);
+    for (uint32_t j = 1; j <= N; ++j) {
         uint32_t acc = 0;
         for (int k = 0; k <= d; ++k)
             if (bit(mu, (size_t)k))
@@ -238,14 +268,16 @@ bool annihilates(const SetP& p, const Poly& mu, const uint32_t* state)
     return true;
 }
 
-// mu for a parameter set: LCM of the minimal polynomials of bit sequences
-// (random states, random linear functionals of the words) until it
-// annihilates fresh random states.
-Poly transition_polynomial(const SetP& p, uint32_t mexp)
+// mu for a parameter set (of MTGP or of the original MT): LCM of the minimal
+// polynomials of bit sequences (random states, random linear functionals of
+// the words) until it annihilates fresh random states.
+template <class Rec>
+Poly transition_polynomial(const Rec& p, uint32_t mexp)
 {
-    std::mt19937_64 rng(0x9E3779B97F4A7C15ull ^ ((uint64_t)p.pos << 32) ^ p.sh1 ^ ((uint64_t)p.rec[1] << 7));
+    std::mt19937_64 rng(rng_seed(p));
+    const uint32_t N = window_words(p);
     auto random_state = [&](std::vector<uint32_t>& st) {
-        st.resize(p.n);
+        st.resize(N);
         for (auto& v : st)
             v = (uint32_t)rng();
     };
@@ -260,14 +292,14 @@ Poly transition_polynomial(const SetP& p, uint32_t mexp)
         // in the oldest word or in the low bits of the next one, so a
         // functional of a single word would not see every part of the
         // transition.
-        std::vector<uint32_t> f(p.n);
+        std::vector<uint32_t> f(N);
         for (auto& v : f)
             v = (uint32_t)rng();
-        f[0] &= p.mask;
+        f[0] &= oldest_mask(p);
         std::vector<uint8_t> bits(len);
         for (size_t i = 0; i < len; ++i) {
             uint32_t acc = 0;
-            for (uint32_t j = 0; j < p.n; ++j)
+            for (uint32_t j = 0; j < N; ++j)
                 acc ^= seq[i + j] & f[j];
             bits[i] = (uint8_t)__builtin_parity(acc);
         }
@@ -323,7 +355,13 @@ std::vector<uint32_t> key_of(const SetP& p)
     return k;
 }
 
-const Poly* cached_mu(const SetP& p, uint32_t mexp)
+std::vector<uint32_t> key_of(const MtRec& p)
+{
+    return {0xFFFFFFFFu, p.n, p.m, p.upper, p.a};   // first word: never an MTGP state size
+}
+
+template <class Rec>
+const Poly* cached_mu(const Rec& p, uint32_t mexp)
 {
     const auto key = key_of(p);
     {
@@ -514,18 +552,12 @@ extern "C" mtgp_status mtgp_params_minpoly(mtgp_params_t params, uint64_t* words
     }
 }
 
-extern "C" mtgp_status mtgp_params_period_check(mtgp_params_t params, void* cuda_stream, int32_t* irreducible)
+// Rabin's irreducibility test of mu for exponent n on the device (sets
+// *irreducible; 0 also when deg mu != n or mu cannot be primitive).
+static mtgp_status rabin_irreducible(const Poly& mu, uint32_t n, void* cuda_stream, int32_t* irreducible)
 {
     try {
-        if (!params || !irreducible)
-            return fail(MTGP_EINVAL, "null argument");
         *irreducible = 0;
-        const uint32_t n = params->d.mexp;
-        const SetP p = set_of(params->k, nullptr);
-        const Poly* mup = cached_mu(p, n);
-        if (!mup)
-            return fail(MTGP_EINVAL, "no annihilating polynomial found for this parameter set");
-        const Poly& mu = *mup;
         const int D = degree(mu);
         // a full-period transition needs deg mu = Mexp, mu(0) = 1, mu(1) = 1
         int terms = 0;
@@ -623,6 +655,89 @@ extern "C" mtgp_status mtgp_params_period_check(mtgp_params_t params, void* cuda
         }
         *irreducible = 1;
         return ok();
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+extern "C" mtgp_status mtgp_params_period_check(mtgp_params_t params, void* cuda_stream, int32_t* irreducible)
+{
+    try {
+        if (!params || !irreducible)
+            return fail(MTGP_EINVAL, "null argument");
+        *irreducible = 0;
+        const Poly* mu = cached_mu(set_of(params->k, nullptr), params->d.mexp);
+        if (!mu)
+            return fail(MTGP_EINVAL, "no annihilating polynomial found for this parameter set");
+        return rabin_irreducible(*mu, params->d.mexp, cuda_stream, irreducible);
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same polynomial and period check for the original Mersenne Twister
+// (the comparison generator of Sec. 5.3): its window transition also maps the
+// unused low r bits of the oldest word to zero, so mu is found the same way.
+// ---------------------------------------------------------------------------
+static mtgp_status mt_rec(const mtgp_mt_params* q, MtRec* out)
+{
+    if (!q)
+        return fail(MTGP_EINVAL, "null argument");
+    if (q->n < 2 || q->n > 4096 || q->m < 1 || q->m > q->n - 1 || q->r > 31 ||
+        (uint64_t)32 * q->n - q->r != q->p)
+        return fail(MTGP_EINVAL, "parameter set out of range (p %u, n %u, m %u, r %u)", q->p, q->n, q->m,
+                    q->r);
+    out->n = q->n;
+    out->m = q->m;
+    out->upper = 0xFFFFFFFFu << q->r;
+    out->a = q->a;
+    return MTGP_OK;
+}
+
+extern "C" mtgp_status mtgp_mt_params_minpoly(const mtgp_mt_params* params, uint64_t* words,
+                                              uint32_t cap_words, int32_t* degree_out)
+{
+    try {
+        MtRec p;
+        if (!degree_out)
+            return fail(MTGP_EINVAL, "null argument");
+        mtgp_status st = mt_rec(params, &p);
+        if (st != MTGP_OK)
+            return st;
+        const Poly* mu = cached_mu(p, params->p);
+        if (!mu)
+            return fail(MTGP_EINVAL, "no annihilating polynomial found for this parameter set");
+        const int d = degree(*mu);
+        *degree_out = d;
+        const uint32_t need = (uint32_t)(d / 64 + 1);
+        if (words) {
+            if (cap_words < need)
+                return fail(MTGP_EINVAL, "need %u words", need);
+            std::fill(words, words + cap_words, 0ull);
+            std::copy(mu->begin(), mu->end(), words);
+        }
+        return ok();
+    } catch (const std::bad_alloc&) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    }
+}
+
+extern "C" mtgp_status mtgp_mt_params_period_check(const mtgp_mt_params* params, void* cuda_stream,
+                                                   int32_t* irreducible)
+{
+    try {
+        MtRec p;
+        if (!irreducible)
+            return fail(MTGP_EINVAL, "null argument");
+        *irreducible = 0;
+        mtgp_status st = mt_rec(params, &p);
+        if (st != MTGP_OK)
+            return st;
+        const Poly* mu = cached_mu(p, params->p);
+        if (!mu)
+            return fail(MTGP_EINVAL, "no annihilating polynomial found for this parameter set");
+        return rabin_irreducible(*mu, params->p, cuda_stream, irreducible);
     } catch (const std::bad_alloc&) {
         return fail(MTGP_ENOMEM, "host allocation failed");
     }

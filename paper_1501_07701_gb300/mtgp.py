@@ -141,6 +141,9 @@ _SIGS = {
     "mtgp_mt_get_statuses": [_VP, _U32P, _VP],
     "mtgp_mt_generate": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP, _VP],
     "mtgp_mt_check": [_VP, _VP],
+    "mtgp_mt_params_minpoly": [ctypes.POINTER(MtParams), _U64P, ctypes.c_uint32,
+                               ctypes.POINTER(ctypes.c_int32)],
+    "mtgp_mt_params_period_check": [ctypes.POINTER(MtParams), _VP, ctypes.POINTER(ctypes.c_int32)],
     "mtgp_mt_free": [_VP],
     "mtgp_last_error": [],
     "mtgp_version": [],
@@ -667,3 +670,23 @@ def mtgp_mt_generate(mt: MtStreams, stream_ids, counts, fmt, out, stream=None):
 
 def mtgp_mt_check(mt: MtStreams, stream=None):
     _call("mtgp_mt_check", mt.handle, _stream_handle(stream))
+
+
+def mtgp_mt_params_minpoly(params: MtParams) -> np.ndarray:
+    """Coefficients (uint8, index = power of t) of the set's transition polynomial."""
+    q = MtParams(*[getattr(params, f) for f, _ in MtParams._fields_])
+    d = ctypes.c_int32()
+    _call("mtgp_mt_params_minpoly", ctypes.byref(q), None, 0, ctypes.byref(d))
+    words = np.zeros(d.value // 64 + 1, dtype=np.uint64)
+    _call("mtgp_mt_params_minpoly", ctypes.byref(q), _p64(words), words.size, ctypes.byref(d))
+    bits = np.unpackbits(words.view(np.uint8), bitorder="little")
+    return bits[:d.value + 1].copy()
+
+
+def mtgp_mt_params_period_check(params: MtParams, stream=None) -> bool:
+    """True if the set's transition polynomial has degree p and is irreducible
+    (for a Mersenne-prime p: period 2^p - 1)."""
+    q = MtParams(*[getattr(params, f) for f, _ in MtParams._fields_])
+    r = ctypes.c_int32()
+    _call("mtgp_mt_params_period_check", ctypes.byref(q), _stream_handle(stream), ctypes.byref(r))
+    return bool(r.value)

@@ -257,3 +257,83 @@ def test_period_check_of_benchmark_sets(_cuda):
         verdict = mtgp.mtgp_params_period_check(mtgp.mtgp_params_generate(mexp, workloads.PARAM_SEED))
         print("Mexp %d seed 0x5EED: full period %s" % (mexp, verdict))
         assert verdict in (True, False)
+
+
+# ---------------------------------------------------------------------------
+# The original MT (comparison generator of Sec. 5.3): the same polynomial and
+# period check, pinned at full size by MT19937's published characteristic
+# polynomial.
+# ---------------------------------------------------------------------------
+def _mt_words(oq, state, count):
+    import oracle.mt as omt
+    out = [np.asarray(state, np.uint32)]
+    s = np.asarray(state, np.uint32).copy()
+    for _ in range((count + oq.n - 1) // oq.n):
+        _, s = omt.generate(oq, s, oq.n)
+        out.append(s.copy())
+    return np.concatenate(out)[:oq.n + count]
+
+
+def _mt_pair(p, seed):
+    import oracle.mt as omt
+    if p == 19937:
+        return mtgp.mtgp_mt_params_mt19937(), omt.params_mt19937()
+    return mtgp.mtgp_mt_params_generate(p, seed), omt.params_generate(p, seed)
+
+
+def test_mt19937_polynomial_is_the_published_one():
+    """MT19937's characteristic polynomial has degree 19937 and 135 nonzero
+    coefficients (Panneton, L'Ecuyer and Matsumoto, ACM TOMS 32(1), 2006,
+    which lists N1 = 135 for MT19937), and a nonzero constant term."""
+    mtgp.load_library()
+    mu = mtgp.mtgp_mt_params_minpoly(mtgp.mtgp_mt_params_mt19937())
+    assert mu.size - 1 == 19937 and mu[0] == 1 and int(mu.sum()) == 135
+
+
+@pytest.mark.parametrize("p,seed", [(19937, 0), (3217, workloads.PARAM_SEED), (3217, 7), (521, 3)])
+def test_mt_minpoly_annihilates_oracle_sequences(p, seed):
+    mtgp.load_library()
+    mq, oq = _mt_pair(p, seed)
+    mu = mtgp.mtgp_mt_params_minpoly(mq)
+    d = mu.size - 1
+    assert mu[d] == 1 and d <= p
+    ks = np.nonzero(mu)[0]
+    rng = np.random.default_rng(seed + p)
+    st = rng.integers(0, 2 ** 32, oq.n, dtype=np.uint64).astype(np.uint32)
+    x = _mt_words(oq, st, d + 2)
+    for j in range(1, oq.n + 1):
+        assert np.bitwise_xor.reduce(x[ks + j]) == 0, "j = %d" % j
+    short = ks[ks < d]
+    assert any(np.bitwise_xor.reduce(x[short + j]) != 0 for j in range(1, oq.n + 1))
+
+
+@gpu
+def test_mt19937_period_check_is_positive(_cuda):
+    """The 1998 paper proves period 2^19937 - 1 for MT19937: a full-size
+    known positive for the device's Rabin test."""
+    assert mtgp.mtgp_mt_params_period_check(mtgp.mtgp_mt_params_mt19937())
+
+
+@gpu
+@pytest.mark.parametrize("p,n", [(61, 2), (89, 3), (107, 4), (127, 4), (100, 4)])
+def test_mt_period_check_agrees_with_ddf(_cuda, p, n):
+    """Toy MT sets with random a, m and tempering (the tempering does not
+    enter the polynomial); at least one full-period set per Mersenne exponent
+    is searched for, so both verdicts are exercised."""
+    import oracle.mt as omt
+    rng = np.random.default_rng(2000 + p)
+    seen = set()
+    for trial in range(400):
+        f = dict(p=p, n=n, r=32 * n - p, m=int(rng.integers(1, n)),
+                 a=int(rng.integers(0, 2 ** 32)) | 0x80000000, u=11, s=7, t=15, l=18,
+                 b=0x9D2C5680, c=0xEFC60000)
+        q = mtgp.MtParams(*[f[k] for k, _ in mtgp.MtParams._fields_])
+        mu = mtgp.mtgp_mt_params_minpoly(q)
+        expect = mu.size - 1 == p and _irreducible_ddf(mu)
+        got = mtgp.mtgp_mt_params_period_check(q)
+        assert got == expect, f
+        seen.add(got)
+        if trial >= 12 and (True in seen or p == 100):
+            break
+    assert True in seen or p == 100    # 100 is composite: no irreducible degree-100 mu is needed
+    assert omt.params_from_fields(**f).n == n
