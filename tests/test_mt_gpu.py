@@ -223,3 +223,28 @@ def test_multi_set_argument_errors():
         mtgp.mtgp_mt_init_multi([a, b], [0, 1, 0, 1], seeds)          # state sizes differ
     with pytest.raises(mtgp.MtgpError):
         mtgp.mtgp_mt_init_multi([a, a], [0, 1, 2, 0], seeds)          # index >= n_sets
+
+
+def test_single_request_beyond_2p32():
+    """Maximum size: one MT19937 request of 2^32 + 1000 numbers from one
+    stream (17 GB of output; step and output indices past 32 bits).  The
+    oracle runs the same 2^32 + 1000 numbers in 2^28-number chunks; the first
+    2^20 outputs, the last 1000 and the final state must match."""
+    mp, op = _set("mt19937")
+    big = (1 << 32) + 1000
+    mt = mtgp.mtgp_mt_init(mp, np.array([4357, 1], np.uint32))
+    s0 = mtgp.mtgp_mt_get_statuses(mt)[0]
+    out = torch.empty(big, dtype=torch.int32, device="cuda")
+    mtgp.mtgp_mt_generate(mt, [0], [big], mtgp.MTGP_U32, out)
+    mtgp.mtgp_mt_check(mt)
+    first, s = omt.generate(op, s0, 1 << 20)
+    np.testing.assert_array_equal(out[:1 << 20].cpu().numpy().view(np.uint32), first)
+    left = big - (1 << 20)
+    while left > 1000:
+        step = min(1 << 28, left - 1000)
+        _, s = omt.generate(op, s, step)
+        left -= step
+    tail, s = omt.generate(op, s, 1000)
+    np.testing.assert_array_equal(out[big - 1000:].cpu().numpy().view(np.uint32), tail)
+    np.testing.assert_array_equal(mtgp.mtgp_mt_get_statuses(mt)[0], s)
+    del out
