@@ -593,6 +593,8 @@ def run_quality_sweep(args):
                     "pass_both": float((ok_g & ok_h).mean()),
                     "gap_p_below_1e-3": int((pg < 1e-3).sum()),
                     "hamming_p_below_1e-3": int((ph < 1e-3).sum()),
+                    "failing_gap_sets": [int(i) for i in np.nonzero(~ok_g)[0]],
+                    "failing_hamming_sets": [int(i) for i in np.nonzero(~ok_h)[0]],
                     "gen_gnum_s": S * C / (e0.elapsed_time(e1) * 1e6),
                     "stats_ms": e1.elapsed_time(e2), "bit_exact_sample": exact}
         del st
