@@ -248,3 +248,17 @@ def test_single_request_beyond_2p32():
     np.testing.assert_array_equal(out[big - 1000:].cpu().numpy().view(np.uint32), tail)
     np.testing.assert_array_equal(mtgp.mtgp_mt_get_statuses(mt)[0], s)
     del out
+
+
+@pytest.mark.parametrize("name", ["mt19937", "p3217", "p521"])
+def test_zero_state_is_a_fixed_point(name):
+    mp, op = _set(name)
+    mt = mtgp.mtgp_mt_init(mp, np.arange(3, dtype=np.uint32))
+    mtgp.mtgp_mt_set_statuses(mt, np.zeros((3, op.n), np.uint32))
+    expect = {mtgp.MTGP_U32: 0, mtgp.MTGP_F32_12: 0x3F800000, mtgp.MTGP_F32_01: 0}
+    counts = np.array([5000, 1, op.n * 3 + 7], np.uint64)
+    for fmt in FMTS:
+        out = torch.full((int(counts.sum()),), -1, dtype=torch.int32, device="cuda")
+        mtgp.mtgp_mt_generate(mt, [0, 1, 2], counts, fmt, out)
+        assert np.all(out.cpu().numpy().view(np.uint32) == expect[fmt]), fmt
+    assert not mtgp.mtgp_mt_get_statuses(mt).any()

@@ -519,3 +519,19 @@ def test_single_request_beyond_2p32():
     _assert_same(out[1 << 32:].cpu().numpy().view(np.uint32), tail, "last 1000")
     _assert_same(mtgp.mtgp_get_statuses(st)[0], s_end, "final state")
     del out
+
+
+@pytest.mark.parametrize("mexp,kernel", [(11213, 0), (11213, 1), (3217, 0)])
+def test_zero_state_is_a_fixed_point(mexp, kernel):
+    """The degenerate case of a linear generator: the all-zero state stays
+    zero and every output is 0 (u32), 1.0f ([1,2)) or 0.0f ([0,1))."""
+    gp, op = _both_params(mexp)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(3, dtype=np.uint32))
+    mtgp.mtgp_set_launch_config(st, warps_per_cta=4, words_per_lane=2 if mexp == 3217 else 4,
+                                kernel=kernel)
+    mtgp.mtgp_set_statuses(st, np.zeros((3, op.n), np.uint32))
+    expect = {mtgp.MTGP_U32: 0, mtgp.MTGP_F32_12: 0x3F800000, mtgp.MTGP_F32_01: 0}
+    for fmt in FMTS:
+        out = _gpu_generate(st, [0, 1, 2], [5000, 1, op.n * 3 + 7], fmt)
+        assert np.all(out == expect[fmt]), fmt
+    assert not mtgp.mtgp_get_statuses(st).any()
