@@ -16,6 +16,7 @@
 // store.  The twist and the tempering are register arithmetic; the two left
 // shifts of the tempering run as integer multiplies on the FMA pipe.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <vector>
 
@@ -322,7 +323,10 @@ struct mtgp_mt {
     uint32_t n_streams = 0;
     uint32_t* d_states = nullptr;
     int* d_err = nullptr;
-    TableSlot slot{};
+    // work tables: a ring of pinned upload slots, each reused only after the
+    // launch that read it has finished
+    std::array<TableSlot, 4> slots{};
+    int next_slot = 0;
     int threads = 0;
     size_t smem = 0;
     int grid_cap = 0;   // resident CTAs on the device
@@ -337,9 +341,11 @@ static void destroy_mt(mtgp_mt* h)
     if (!h)
         return;
     DeviceGuard g(h->device);
-    free_table_slot(h->slot);
-    if (h->slot.ev)
-        cudaEventDestroy(h->slot.ev);
+    for (auto& sl : h->slots) {
+        free_table_slot(sl);
+        if (sl.ev)
+            cudaEventDestroy(sl.ev);
+    }
     if (h->d_states)
         cudaFree(h->d_states);
     if (h->d_err)
@@ -461,8 +467,9 @@ static mtgp_status init_handle(const mtgp_mt_params* sets, uint32_t n_sets, cons
             return bail(e, "cudaMalloc(error word)");
         if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), s)) != cudaSuccess)
             return bail(e, "cudaMemsetAsync");
-        if ((e = cudaEventCreateWithFlags(&h->slot.ev, cudaEventDisableTiming)) != cudaSuccess)
-            return bail(e, "cudaEventCreate");
+        for (auto& sl : h->slots)
+            if ((e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess)
+                return bail(e, "cudaEventCreate");
         // launch geometry: kWarpsPerCta warps per CTA, as many CTAs as fit
         const void* fn = mt_kernel_ptr(h->K);
         h->threads = 32 * kWarpsPerCta;
@@ -579,7 +586,8 @@ extern "C" mtgp_status mtgp_mt_generate(mtgp_mt_t h, const uint32_t* ids, const 
             return fail(MTGP_EINVAL, "output pointer null or not 4-byte aligned");
         DeviceGuard g(h->device);
         cudaStream_t s = (cudaStream_t)cuda_stream;
-        TableSlot& sl = h->slot;
+        TableSlot& sl = h->slots[h->next_slot];
+        h->next_slot = (h->next_slot + 1) % (int)h->slots.size();
         if (sl.ev_recorded) {
             MT_TRY(cudaEventSynchronize(sl.ev), "cudaEventSynchronize(table slot)");
             sl.ev_recorded = false;
