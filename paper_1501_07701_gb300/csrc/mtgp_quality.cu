@@ -23,25 +23,20 @@ using namespace mtgp;
 
 namespace {
 
-constexpr uint32_t kChunk = 1u << 16;       // values per gap-test work unit (one warp)
+constexpr uint32_t kChunk = 1u << 14;       // values per gap-test work unit
 constexpr uint32_t kMaxT = 1023;            // largest pooled gap class
 constexpr uint32_t kMaxClasses = 16;        // largest number of weight classes
 constexpr int kWarps = 8;                   // warps per CTA of both kernels
 
-struct GapChunk {
-    uint64_t start;   // first value (element offset into `values`)
-    uint32_t len;     // values in the chunk (<= kChunk)
-    uint32_t seq;     // sequence it belongs to
-};
-
 // Per chunk: the run of non-visits before its first visit (the whole length
-// if it has none), the run after its last visit, and whether it has a visit.
-// Gaps that cross chunk boundaries are completed on the host from these.
+// if it has none), the run after its last visit, whether it has a visit, and
+// its length.  Gaps that cross chunk boundaries are completed from these by
+// the stitch kernel.
 struct GapEdge {
     uint32_t prefix;
     uint32_t suffix;
     uint32_t has_visit;
-    uint32_t pad;
+    uint32_t pad;   // chunk length
 };
 
 __device__ __forceinline__ bool field_is_zero(uint32_t x, uint32_t r, uint32_t width)
@@ -50,81 +45,164 @@ __device__ __forceinline__ bool field_is_zero(uint32_t x, uint32_t r, uint32_t w
     return ((x << r) >> (32u - width)) == 0u;
 }
 
-// One warp per chunk.  Per group of 32 consecutive values the visits form a
-// ballot mask B; a visiting lane's gap is the distance to the nearest lower
-// visiting lane, or the carried run D plus its lane index if it is the
-// group's first visit.  The ballot and every shuffle run in warp-uniform
-// control flow; the per-lane branch holds only shared-memory atomics.
+// Work units: sequence i is cut into ceil(counts[i] / kChunk) chunks; chunk
+// c of the launch is found from the prefix sums of those chunk counts.  Warps
+// claim runs of kRun consecutive chunks from an atomic counter, so a warp's
+// consecutive chunks mostly share a sequence and its histogram, which is
+// flushed to global memory only when the sequence changes.  Per group of 32
+// consecutive values the visits form a ballot mask B; a visiting lane's gap
+// is the distance to the nearest lower visiting lane, or the carried run D
+// plus its lane index if it is the group's first visit (the first visit of a
+// chunk is left to the stitch kernel).  Loads run a round ahead of the scan:
+// the 16 groups of the next round are in flight while the current round is
+// scanned.  The ballot and every shuffle run in warp-uniform control flow;
+// the per-lane branch holds only shared-memory atomics.
+constexpr uint32_t kG = 16;     // groups of 32 values per load round
+constexpr uint32_t kRun = 4;    // chunks per claim
+
+__device__ __forceinline__ void gap_flush(uint32_t* h, uint32_t t, unsigned long long* hs, uint32_t lane)
+{
+    __syncwarp();
+    for (uint32_t i = lane; i <= t; i += 32u) {
+        if (h[i])
+            atomicAdd(hs + i, (unsigned long long)h[i]);
+        h[i] = 0u;
+    }
+    __syncwarp();
+}
+
+// Sequence holding chunk c: the last i with chunk_base[i] <= c.
+__device__ __forceinline__ uint32_t chunk_seq(const uint64_t* __restrict__ chunk_base, uint32_t n_seq,
+                                              uint64_t c)
+{
+    uint32_t lo = 0, hi = n_seq;
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (chunk_base[mid] <= c)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(kWarps * 32) mtgp_gap_kernel(const uint32_t* __restrict__ values,
-                                                              const GapChunk* __restrict__ chunks,
-                                                              uint32_t n_chunks, uint32_t r, uint32_t b,
-                                                              uint32_t t,
+                                                              const uint64_t* __restrict__ seq_start,
+                                                              const uint64_t* __restrict__ counts,
+                                                              const uint64_t* __restrict__ chunk_base,
+                                                              uint32_t n_seq, uint64_t n_chunks,
+                                                              uint32_t r, uint32_t b, uint32_t t,
+                                                              unsigned long long* __restrict__ claim,
                                                               unsigned long long* __restrict__ hist,
                                                               GapEdge* __restrict__ edges)
 {
-    __shared__ uint32_t h_all[kWarps][kMaxT + 1];
+    extern __shared__ uint32_t h_all[];   // kWarps histograms of t + 1 counts
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint32_t* h = h_all[warp];
-    const uint32_t gwarp = blockIdx.x * kWarps + warp, nwarps = gridDim.x * kWarps;
-    for (uint32_t c = gwarp; c < n_chunks; c += nwarps) {
-        const GapChunk ch = chunks[c];
-        for (uint32_t i = lane; i <= t; i += 32u)
-            h[i] = 0u;
-        __syncwarp();
-        const uint32_t* v = values + ch.start;
-        uint32_t D = 0, P = 0;
-        bool seen = false;
-        // 8 groups of 32 values per round: their loads are all in flight
-        // before the first group is scanned
-        constexpr uint32_t kG = 8;
-        for (uint32_t base0 = 0; base0 < ch.len; base0 += 32u * kG) {
-            uint32_t xs[kG];
-#pragma unroll
-            for (uint32_t g = 0; g < kG; ++g) {
-                const uint32_t idx = base0 + 32u * g + lane;
-                xs[g] = idx < ch.len ? __ldcs(v + idx) : 0u;
+    uint32_t* h = h_all + warp * (t + 1u);
+    for (uint32_t i = lane; i <= t; i += 32u)
+        h[i] = 0u;
+    __syncwarp();
+    uint32_t cur = 0xFFFFFFFFu;
+    for (;;) {
+        unsigned long long c0 = 0;
+        if (lane == 0)
+            c0 = atomicAdd(claim, (unsigned long long)kRun);
+        c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
+        if (c0 >= n_chunks)
+            break;
+        const uint64_t c1 = min((uint64_t)c0 + kRun, n_chunks);
+        uint32_t seq = chunk_seq(chunk_base, n_seq, c0);
+        for (uint64_t c = c0; c < c1; ++c) {
+            while (c >= chunk_base[seq + 1u])
+                ++seq;
+            if (seq != cur) {
+                if (cur != 0xFFFFFFFFu)
+                    gap_flush(h, t, hist + (size_t)cur * (t + 1u), lane);
+                cur = seq;
             }
+            const uint64_t off = (c - chunk_base[seq]) * kChunk;
+            const uint64_t left = counts[seq] - off;
+            const uint32_t len = left < kChunk ? (uint32_t)left : kChunk;
+            const uint32_t* v = values + seq_start[seq] + off;
+            uint32_t D = 0, P = 0;
+            bool seen = false;
+            uint32_t xa[kG];
 #pragma unroll
             for (uint32_t g = 0; g < kG; ++g) {
-                const uint32_t base = base0 + 32u * g;
-                if (base >= ch.len)
-                    break;
-                const bool in = base + lane < ch.len && field_is_zero(xs[g], r, b);
-                const uint32_t B = __ballot_sync(0xFFFFFFFFu, in);
-                if (in) {
-                    const uint32_t below = B & ((1u << lane) - 1u);
-                    if (below) {
-                        const uint32_t gap = lane - (31u - __clz(below)) - 1u;
-                        atomicAdd(&h[min(gap, t)], 1u);
-                    } else if (seen) {
-                        atomicAdd(&h[min(D + lane, t)], 1u);
+                const uint32_t idx = 32u * g + lane;
+                xa[g] = idx < len ? __ldcs(v + idx) : 0u;
+            }
+            for (uint32_t base0 = 0; base0 < len; base0 += 32u * kG) {
+                uint32_t xb[kG];   // the next round, loaded before this one is scanned
+#pragma unroll
+                for (uint32_t g = 0; g < kG; ++g) {
+                    const uint32_t idx = base0 + 32u * (kG + g) + lane;
+                    xb[g] = idx < len ? __ldcs(v + idx) : 0u;
+                }
+#pragma unroll
+                for (uint32_t g = 0; g < kG; ++g) {
+                    const uint32_t base = base0 + 32u * g;
+                    if (base >= len)
+                        break;
+                    const bool in = base + lane < len && field_is_zero(xa[g], r, b);
+                    const uint32_t B = __ballot_sync(0xFFFFFFFFu, in);
+                    if (in) {
+                        const uint32_t below = B & ((1u << lane) - 1u);
+                        if (below) {
+                            const uint32_t gap = lane - (31u - __clz(below)) - 1u;
+                            atomicAdd(&h[min(gap, t)], 1u);
+                        } else if (seen) {
+                            atomicAdd(&h[min(D + lane, t)], 1u);
+                        }
+                    }
+                    const uint32_t nv = min(32u, len - base);
+                    if (B) {
+                        if (!seen)
+                            P = D + (uint32_t)(__ffs(B) - 1);
+                        seen = true;
+                        D = nv - 1u - (31u - __clz(B));
+                    } else {
+                        D += nv;
                     }
                 }
-                const uint32_t nv = min(32u, ch.len - base);
-                if (B) {
-                    if (!seen)
-                        P = D + (uint32_t)(__ffs(B) - 1);
-                    seen = true;
-                    D = nv - 1u - (31u - __clz(B));
-                } else {
-                    D += nv;
-                }
+#pragma unroll
+                for (uint32_t g = 0; g < kG; ++g)
+                    xa[g] = xb[g];
+            }
+            if (lane == 0) {
+                GapEdge e;
+                e.prefix = seen ? P : len;
+                e.suffix = D;
+                e.has_visit = seen ? 1u : 0u;
+                e.pad = len;
+                edges[c] = e;
             }
         }
-        __syncwarp();
-        unsigned long long* hs = hist + (size_t)ch.seq * (t + 1u);
-        for (uint32_t i = lane; i <= t; i += 32u)
-            if (h[i])
-                atomicAdd(hs + i, (unsigned long long)h[i]);
-        if (lane == 0) {
-            GapEdge e;
-            e.prefix = seen ? P : ch.len;
-            e.suffix = D;
-            e.has_visit = seen ? 1u : 0u;
-            e.pad = 0;
-            edges[c] = e;
+    }
+    if (cur != 0xFFFFFFFFu)
+        gap_flush(h, t, hist + (size_t)cur * (t + 1u), lane);
+}
+
+// Gaps that cross chunk boundaries, and each sequence's first gap: one
+// thread per sequence walks its chunks' edges in order.
+__global__ void __launch_bounds__(256) mtgp_gap_stitch_kernel(const uint64_t* __restrict__ chunk_base,
+                                                             uint32_t n_seq, uint32_t t,
+                                                             const GapEdge* __restrict__ edges,
+                                                             unsigned long long* __restrict__ hist)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seq)
+        return;
+    uint64_t run = 0;
+    for (uint64_t c = chunk_base[i]; c < chunk_base[i + 1u]; ++c) {
+        const GapEdge e = edges[c];
+        if (e.has_visit) {
+            const uint64_t gap = run + e.prefix;
+            atomicAdd(hist + (size_t)i * (t + 1u) + (gap < t ? gap : (uint64_t)t), 1ull);
+            run = e.suffix;
+        } else {
+            run += e.pad;   // the chunk's length
         }
-        __syncwarp();
     }
 }
 
@@ -185,14 +263,24 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_hamming_kernel(const uint32_
         }
         const uint32_t* v = values + seq_start[seq] + (p - pair_base[seq]) * 2ull * K;
         uint32_t wa = 0, wb = 0;
-#pragma unroll 4
-        for (uint32_t j = lane; j < 2u * K; j += 32u) {
-            const uint32_t x = __ldcs(v + j);
-            const uint32_t w = __popc((x << r) >> (32u - s));
-            if (j < K)
-                wa += w;
-            else
-                wb += w;
+        // the pair's values in batches of kB per lane, all of a batch in flight
+        constexpr uint32_t kB = 16;
+        for (uint32_t j0 = 0; j0 < 2u * K; j0 += 32u * kB) {
+            uint32_t xs[kB];
+#pragma unroll
+            for (uint32_t q = 0; q < kB; ++q) {
+                const uint32_t j = j0 + 32u * q + lane;
+                xs[q] = j < 2u * K ? __ldcs(v + j) : 0u;
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < kB; ++q) {
+                const uint32_t j = j0 + 32u * q + lane;
+                const uint32_t w = __popc((xs[q] << r) >> (32u - s));
+                if (j < K)
+                    wa += w;
+                else if (j < 2u * K)
+                    wb += w;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -216,12 +304,12 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_hamming_kernel(const uint32_
                 atomicAdd(table + (size_t)seq * C * C + i, (unsigned long long)tab[i]);
 }
 
-int grid_for(const void* fn)
+int grid_for(const void* fn, size_t dyn_smem = 0)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kWarps * 32, dyn_smem);
     return std::max(1, sms * std::max(per, 1));
 }
 
@@ -263,61 +351,53 @@ extern "C" mtgp_status mtgp_gap_histogram(const uint32_t* values, const uint64_t
         if (b < 1 || r + b > 32 || t < 1 || t > kMaxT)
             return fail(MTGP_EINVAL, "need b >= 1, r + b <= 32, 1 <= t <= %u", kMaxT);
         uint64_t total = 0;
-        std::vector<GapChunk> chunks;
-        std::vector<uint64_t> seq_first_chunk(n_seq + 1);
+        std::vector<uint64_t> seq_start(n_seq), chunk_base(n_seq + 1);
+        uint64_t n_chunks = 0;
         for (uint32_t i = 0; i < n_seq; ++i) {
-            seq_first_chunk[i] = chunks.size();
-            for (uint64_t o = 0; o < counts[i]; o += kChunk) {
-                GapChunk c;
-                c.start = total + o;
-                c.len = (uint32_t)std::min<uint64_t>(kChunk, counts[i] - o);
-                c.seq = i;
-                chunks.push_back(c);
-            }
+            seq_start[i] = total;
+            chunk_base[i] = n_chunks;
+            n_chunks += (counts[i] + kChunk - 1) / kChunk;
             total += counts[i];
         }
-        seq_first_chunk[n_seq] = chunks.size();
+        chunk_base[n_seq] = n_chunks;
         std::fill(hist, hist + (size_t)n_seq * (t + 1), 0ull);
         if (total && !values)
             return fail(MTGP_EINVAL, "null values pointer");
-        if (chunks.empty())
+        if (n_chunks == 0)
             return ok();
         cudaStream_t s = (cudaStream_t)cuda_stream;
-        std::vector<GapEdge> edges(chunks.size());
-        {
-            Scratch sc(s);
-            void *d_chunks, *d_hist, *d_edges;
-            const size_t hbytes = (size_t)n_seq * (t + 1) * sizeof(unsigned long long);
-            Q_TRY(sc.alloc(&d_chunks, chunks.size() * sizeof(GapChunk)), "cudaMallocAsync");
-            Q_TRY(sc.alloc(&d_hist, hbytes), "cudaMallocAsync");
-            Q_TRY(sc.alloc(&d_edges, chunks.size() * sizeof(GapEdge)), "cudaMallocAsync");
-            Q_TRY(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(GapChunk),
-                                  cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
-            Q_TRY(cudaMemsetAsync(d_hist, 0, hbytes, s), "cudaMemsetAsync");
-            const int grid = std::min<long long>(grid_for((const void*)mtgp_gap_kernel),
-                                                 ((long long)chunks.size() + kWarps - 1) / kWarps);
-            mtgp_gap_kernel<<<grid, kWarps * 32, 0, s>>>(values, (const GapChunk*)d_chunks,
-                                                          (uint32_t)chunks.size(), r, b, t,
+        Scratch sc(s);
+        void *d_start, *d_counts, *d_base, *d_claim, *d_hist, *d_edges;
+        const size_t hbytes = (size_t)n_seq * (t + 1) * sizeof(unsigned long long);
+        Q_TRY(sc.alloc(&d_start, n_seq * sizeof(uint64_t)), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_counts, n_seq * sizeof(uint64_t)), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_base, (n_seq + 1) * sizeof(uint64_t)), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_claim, sizeof(unsigned long long)), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_hist, hbytes), "cudaMallocAsync");
+        Q_TRY(sc.alloc(&d_edges, n_chunks * sizeof(GapEdge)), "cudaMallocAsync");
+        Q_TRY(cudaMemcpyAsync(d_start, seq_start.data(), n_seq * sizeof(uint64_t), cudaMemcpyHostToDevice, s),
+              "cudaMemcpyAsync");
+        Q_TRY(cudaMemcpyAsync(d_counts, counts, n_seq * sizeof(uint64_t), cudaMemcpyHostToDevice, s),
+              "cudaMemcpyAsync");
+        Q_TRY(cudaMemcpyAsync(d_base, chunk_base.data(), (n_seq + 1) * sizeof(uint64_t),
+                              cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+        Q_TRY(cudaMemsetAsync(d_claim, 0, sizeof(unsigned long long), s), "cudaMemsetAsync");
+        Q_TRY(cudaMemsetAsync(d_hist, 0, hbytes, s), "cudaMemsetAsync");
+        const size_t hsmem = (size_t)kWarps * (t + 1) * sizeof(uint32_t);   // <= 32 KB
+        const int grid = (int)std::min<uint64_t>((uint64_t)grid_for((const void*)mtgp_gap_kernel, hsmem),
+                                                 (n_chunks + kWarps * kRun - 1) / (kWarps * kRun));
+        mtgp_gap_kernel<<<grid, kWarps * 32, hsmem, s>>>(values, (const uint64_t*)d_start,
+                                                          (const uint64_t*)d_counts, (const uint64_t*)d_base,
+                                                          n_seq, n_chunks, r, b, t,
+                                                          (unsigned long long*)d_claim,
                                                           (unsigned long long*)d_hist, (GapEdge*)d_edges);
-            Q_TRY(cudaGetLastError(), "gap kernel launch");
-            Q_TRY(cudaMemcpyAsync(hist, d_hist, hbytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
-            Q_TRY(cudaMemcpyAsync(edges.data(), d_edges, edges.size() * sizeof(GapEdge),
-                                  cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
-            Q_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-        }
-        // gaps that cross chunk boundaries (and each sequence's first gap)
-        for (uint32_t i = 0; i < n_seq; ++i) {
-            uint64_t run = 0;
-            for (uint64_t c = seq_first_chunk[i]; c < seq_first_chunk[i + 1]; ++c) {
-                if (edges[c].has_visit) {
-                    const uint64_t gap = run + edges[c].prefix;
-                    hist[(size_t)i * (t + 1) + std::min<uint64_t>(gap, t)] += 1;
-                    run = edges[c].suffix;
-                } else {
-                    run += chunks[c].len;
-                }
-            }
-        }
+        Q_TRY(cudaGetLastError(), "gap kernel launch");
+        mtgp_gap_stitch_kernel<<<(n_seq + 255) / 256, 256, 0, s>>>((const uint64_t*)d_base, n_seq, t,
+                                                                   (const GapEdge*)d_edges,
+                                                                   (unsigned long long*)d_hist);
+        Q_TRY(cudaGetLastError(), "gap stitch kernel launch");
+        Q_TRY(cudaMemcpyAsync(hist, d_hist, hbytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+        Q_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
         return ok();
     } catch (const std::bad_alloc&) {
         return fail(MTGP_ENOMEM, "host allocation failed");

@@ -2,7 +2,7 @@
 
 Counts are integers, so the GPU histograms and tables must equal the
 oracle's exactly, per sequence, including gaps that cross the kernel's
-65 536-value work units and sequences of every length.
+16 384-value work units and sequences of every length.
 """
 import numpy as np
 import pytest
@@ -12,7 +12,7 @@ from paper_1501_07701_gb300 import mtgp, quality, workloads
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-CHUNK = 1 << 16
+CHUNK = 1 << 14
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -54,7 +54,7 @@ def test_gap_histogram_matches_oracle(r, b, t):
 
 
 def test_gap_histogram_visits_at_work_unit_edges():
-    """Visits placed at and around the 65 536-value work-unit boundaries, a
+    """Visits placed at and around the 16 384-value work-unit boundaries, a
     work unit without any visit, and a long first gap."""
     n = 5 * CHUNK + 9
     x = np.full(n, 0xFFFFFFFF, np.uint32)
