@@ -39,26 +39,20 @@ struct GapEdge {
     uint32_t pad;   // chunk length
 };
 
-__device__ __forceinline__ bool field_is_zero(uint32_t x, uint32_t r, uint32_t width)
-{
-    // the `width` bits after the r dropped leading bits (r + width <= 32, width >= 1)
-    return ((x << r) >> (32u - width)) == 0u;
-}
-
 // Work units: sequence i is cut into ceil(counts[i] / kChunk) chunks; chunk
 // c of the launch is found from the prefix sums of those chunk counts.  Warps
-// claim runs of kRun consecutive chunks from an atomic counter, so a warp's
+// claim runs of `run` consecutive chunks from an atomic counter, so a warp's
 // consecutive chunks mostly share a sequence and its histogram, which is
 // flushed to global memory only when the sequence changes.  Per group of 32
 // consecutive values the visits form a ballot mask B; a visiting lane's gap
 // is the distance to the nearest lower visiting lane, or the carried run D
 // plus its lane index if it is the group's first visit (the first visit of a
-// chunk is left to the stitch kernel).  Loads run a round ahead of the scan:
+// chunk is left to the stitch kernel); both cases are one expression,
+// gap = lane - 1 - prev with prev = -1 - D when no lower lane visits.  Loads run a round ahead of the scan:
 // the 16 groups of the next round are in flight while the current round is
 // scanned.  The ballot and every shuffle run in warp-uniform control flow;
 // the per-lane branch holds only shared-memory atomics.
 constexpr uint32_t kG = 16;     // groups of 32 values per load round
-constexpr uint32_t kRun = 4;    // chunks per claim
 
 __device__ __forceinline__ void gap_flush(uint32_t* h, uint32_t t, unsigned long long* hs, uint32_t lane)
 {
@@ -91,13 +85,14 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_gap_kernel(const uint32_t* _
                                                               const uint64_t* __restrict__ counts,
                                                               const uint64_t* __restrict__ chunk_base,
                                                               uint32_t n_seq, uint64_t n_chunks,
-                                                              uint32_t r, uint32_t b, uint32_t t,
+                                                              uint32_t run, uint32_t fmask, uint32_t t,
                                                               unsigned long long* __restrict__ claim,
                                                               unsigned long long* __restrict__ hist,
                                                               GapEdge* __restrict__ edges)
 {
     extern __shared__ uint32_t h_all[];   // kWarps histograms of t + 1 counts
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lower = (1u << lane) - 1u;   // lanes below this one
     uint32_t* h = h_all + warp * (t + 1u);
     for (uint32_t i = lane; i <= t; i += 32u)
         h[i] = 0u;
@@ -106,11 +101,11 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_gap_kernel(const uint32_t* _
     for (;;) {
         unsigned long long c0 = 0;
         if (lane == 0)
-            c0 = atomicAdd(claim, (unsigned long long)kRun);
+            c0 = atomicAdd(claim, (unsigned long long)run);
         c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
         if (c0 >= n_chunks)
             break;
-        const uint64_t c1 = min((uint64_t)c0 + kRun, n_chunks);
+        const uint64_t c1 = min((uint64_t)c0 + run, n_chunks);
         uint32_t seq = chunk_seq(chunk_base, n_seq, c0);
         for (uint64_t c = c0; c < c1; ++c) {
             while (c >= chunk_base[seq + 1u])
@@ -144,26 +139,18 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_gap_kernel(const uint32_t* _
                     const uint32_t base = base0 + 32u * g;
                     if (base >= len)
                         break;
-                    const bool in = base + lane < len && field_is_zero(xa[g], r, b);
+                    const bool in = (xa[g] & fmask) == 0u && base + lane < len;
                     const uint32_t B = __ballot_sync(0xFFFFFFFFu, in);
-                    if (in) {
-                        const uint32_t below = B & ((1u << lane) - 1u);
-                        if (below) {
-                            const uint32_t gap = lane - (31u - __clz(below)) - 1u;
-                            atomicAdd(&h[min(gap, t)], 1u);
-                        } else if (seen) {
-                            atomicAdd(&h[min(D + lane, t)], 1u);
-                        }
-                    }
+                    const uint32_t below = B & lower;
+                    // position of the previous visit (-1 - D: D non-visits before this group)
+                    const int prev = below ? 31 - __clz(below) : -1 - (int)D;
+                    if (in && (below || seen))
+                        atomicAdd(&h[min((uint32_t)((int)lane - 1 - prev), t)], 1u);
                     const uint32_t nv = min(32u, len - base);
-                    if (B) {
-                        if (!seen)
-                            P = D + (uint32_t)(__ffs(B) - 1);
-                        seen = true;
-                        D = nv - 1u - (31u - __clz(B));
-                    } else {
-                        D += nv;
-                    }
+                    const uint32_t hiB = 31u - __clz(B);
+                    P = (!seen && B) ? D + (uint32_t)(__ffs(B) - 1) : P;
+                    seen = seen || B;
+                    D = B ? nv - 1u - hiB : D + nv;
                 }
 #pragma unroll
                 for (uint32_t g = 0; g < kG; ++g)
@@ -214,7 +201,7 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_hamming_kernel(const uint32_
                                                                   const uint64_t* __restrict__ seq_start,
                                                                   const uint64_t* __restrict__ pair_base,
                                                                   uint32_t n_seq, uint64_t n_pairs,
-                                                                  uint32_t r, uint32_t s, uint32_t K,
+                                                                  uint32_t fmask, uint32_t K,
                                                                   const uint32_t* __restrict__ bounds,
                                                                   uint32_t n_bounds,
                                                                   unsigned long long* __restrict__ table)
@@ -275,7 +262,7 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_hamming_kernel(const uint32_
 #pragma unroll
             for (uint32_t q = 0; q < kB; ++q) {
                 const uint32_t j = j0 + 32u * q + lane;
-                const uint32_t w = __popc((xs[q] << r) >> (32u - s));
+                const uint32_t w = __popc(xs[q] & fmask);
                 if (j < K)
                     wa += w;
                 else if (j < 2u * K)
@@ -385,10 +372,15 @@ extern "C" mtgp_status mtgp_gap_histogram(const uint32_t* values, const uint64_t
         Q_TRY(cudaMemsetAsync(d_hist, 0, hbytes, s), "cudaMemsetAsync");
         const size_t hsmem = (size_t)kWarps * (t + 1) * sizeof(uint32_t);   // <= 32 KB
         const int grid = (int)std::min<uint64_t>((uint64_t)grid_for((const void*)mtgp_gap_kernel, hsmem),
-                                                 (n_chunks + kWarps * kRun - 1) / (kWarps * kRun));
+                                                 (n_chunks + kWarps - 1) / kWarps);
+        // chunks per claim: about four claims per warp, at most 16 chunks
+        const uint64_t warps = (uint64_t)grid * kWarps;
+        const uint32_t run = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(16, n_chunks / (4 * warps)));
+        // the b bits after the r dropped leading bits
+        const uint32_t fmask = (uint32_t)((((1ull << b) - 1ull) << (32u - r - b)) & 0xFFFFFFFFull);
         mtgp_gap_kernel<<<grid, kWarps * 32, hsmem, s>>>(values, (const uint64_t*)d_start,
                                                           (const uint64_t*)d_counts, (const uint64_t*)d_base,
-                                                          n_seq, n_chunks, r, b, t,
+                                                          n_seq, n_chunks, run, fmask, t,
                                                           (unsigned long long*)d_claim,
                                                           (unsigned long long*)d_hist, (GapEdge*)d_edges);
         Q_TRY(cudaGetLastError(), "gap kernel launch");
@@ -451,8 +443,10 @@ extern "C" mtgp_status mtgp_hamming_pairs(const uint32_t* values, const uint64_t
         Q_TRY(cudaMemsetAsync(d_table, 0, tbytes, st), "cudaMemsetAsync");
         const int grid = (int)std::min<uint64_t>((uint64_t)grid_for((const void*)mtgp_hamming_kernel),
                                                  (pairs + kWarps - 1) / kWarps);
+        // the s bits after the r dropped leading bits
+        const uint32_t fmask = (uint32_t)((((1ull << s) - 1ull) << (32u - r - s)) & 0xFFFFFFFFull);
         mtgp_hamming_kernel<<<grid, kWarps * 32, 0, st>>>(values, (const uint64_t*)d_start,
-                                                           (const uint64_t*)d_base, n_seq, pairs, r, s, K,
+                                                           (const uint64_t*)d_base, n_seq, pairs, fmask, K,
                                                            (const uint32_t*)d_bounds, n_bounds,
                                                            (unsigned long long*)d_table);
         Q_TRY(cudaGetLastError(), "Hamming kernel launch");
