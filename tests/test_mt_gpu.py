@@ -262,3 +262,15 @@ def test_zero_state_is_a_fixed_point(name):
         mtgp.mtgp_mt_generate(mt, [0, 1, 2], counts, fmt, out)
         assert np.all(out.cpu().numpy().view(np.uint32) == expect[fmt]), fmt
     assert not mtgp.mtgp_mt_get_statuses(mt).any()
+
+
+@pytest.mark.parametrize("p", [521, 3217, 19937])
+def test_forty_parameter_seeds(p):
+    """Forty seed-generated original-MT sets per exponent against the oracle."""
+    for pseed in range(100, 140):
+        mp, op = mtgp.mtgp_mt_params_generate(p, pseed), omt.params_generate(p, pseed)
+        assert mp.as_dict() == op.as_dict()
+        mt, got, ref, ref_states = _run(mp, op, np.array([pseed, 7, 8], np.uint32), [0, 1, 2, 0],
+                                        [op.n * 5 + 3, 4097, 1, 333], mtgp.MTGP_U32)
+        np.testing.assert_array_equal(got, ref, err_msg="p %d seed %d" % (p, pseed))
+        np.testing.assert_array_equal(mtgp.mtgp_mt_get_statuses(mt), ref_states)

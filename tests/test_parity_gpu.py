@@ -535,3 +535,19 @@ def test_zero_state_is_a_fixed_point(mexp, kernel):
         out = _gpu_generate(st, [0, 1, 2], [5000, 1, op.n * 3 + 7], fmt)
         assert np.all(out == expect[fmt]), fmt
     assert not mtgp.mtgp_get_statuses(st).any()
+
+
+@pytest.mark.parametrize("mexp", [3217, 11213, 23209])
+def test_forty_parameter_seeds(mexp):
+    """Forty seed-generated sets per exponent (pos, shifts and tables all
+    drawn anew), default launch shape, ragged requests, against the oracle."""
+    for pseed in range(100, 140):
+        gp, op = _both_params(mexp, pseed)
+        st = mtgp.mtgp_init_statuses(gp, np.array([pseed, 7, 8], np.uint32))
+        states = np.stack([oracle.init_state(op, s) for s in (pseed, 7, 8)])
+        ids = np.array([0, 1, 2, 0], np.uint32)
+        counts = np.array([op.n * 5 + 3, 4097, 1, 333], np.uint64)
+        out = _gpu_generate(st, ids, counts)
+        ref, states = oracle.generate_many(op, states, ids, counts, 0, THREADS)
+        _assert_same(out, ref, "mexp %d seed %d" % (mexp, pseed))
+        _assert_same(mtgp.mtgp_get_statuses(st), states)
