@@ -48,11 +48,13 @@ struct GapEdge {
 // is the distance to the nearest lower visiting lane, or the carried run D
 // plus its lane index if it is the group's first visit (the first visit of a
 // chunk is left to the stitch kernel); both cases are one expression,
-// gap = lane - 1 - prev with prev = -1 - D when no lower lane visits.  Loads run a round ahead of the scan:
-// the 16 groups of the next round are in flight while the current round is
-// scanned.  The ballot and every shuffle run in warp-uniform control flow;
-// the per-lane branch holds only shared-memory atomics.
-constexpr uint32_t kG = 16;     // groups of 32 values per load round
+// gap = lane - 1 - prev with prev = -1 - D when no lower lane visits.  Loads
+// run a round ahead of the scan: the kG groups of the next round are in
+// flight while the current round is scanned, and rounds with every value
+// present are scanned without per-lane bounds checks.  The ballot and every
+// shuffle run in warp-uniform control flow; the per-lane branch holds only
+// shared-memory atomics.
+constexpr uint32_t kG = 8;      // groups of 32 values per load round
 
 __device__ __forceinline__ void gap_flush(uint32_t* h, uint32_t t, unsigned long long* hs, uint32_t lane)
 {
@@ -127,35 +129,44 @@ __global__ void __launch_bounds__(kWarps * 32) mtgp_gap_kernel(const uint32_t* _
                 const uint32_t idx = 32u * g + lane;
                 xa[g] = idx < len ? __ldcs(v + idx) : 0u;
             }
-            for (uint32_t base0 = 0; base0 < len; base0 += 32u * kG) {
-                uint32_t xb[kG];   // the next round, loaded before this one is scanned
-#pragma unroll
-                for (uint32_t g = 0; g < kG; ++g) {
-                    const uint32_t idx = base0 + 32u * (kG + g) + lane;
-                    xb[g] = idx < len ? __ldcs(v + idx) : 0u;
-                }
+            // scans one round; `full`: all 32 kG values are present (no per-lane checks)
+            auto scan = [&](const uint32_t (&x)[kG], uint32_t base0, bool full) {
 #pragma unroll
                 for (uint32_t g = 0; g < kG; ++g) {
                     const uint32_t base = base0 + 32u * g;
-                    if (base >= len)
+                    if (!full && base >= len)
                         break;
-                    const bool in = (xa[g] & fmask) == 0u && base + lane < len;
+                    const bool in = (x[g] & fmask) == 0u && (full || base + lane < len);
                     const uint32_t B = __ballot_sync(0xFFFFFFFFu, in);
                     const uint32_t below = B & lower;
                     // position of the previous visit (-1 - D: D non-visits before this group)
                     const int prev = below ? 31 - __clz(below) : -1 - (int)D;
                     if (in && (below || seen))
                         atomicAdd(&h[min((uint32_t)((int)lane - 1 - prev), t)], 1u);
-                    const uint32_t nv = min(32u, len - base);
+                    const uint32_t nv = full ? 32u : min(32u, len - base);
                     const uint32_t hiB = 31u - __clz(B);
                     P = (!seen && B) ? D + (uint32_t)(__ffs(B) - 1) : P;
                     seen = seen || B;
                     D = B ? nv - 1u - hiB : D + nv;
                 }
+            };
+            const uint32_t nfull = len / (32u * kG);   // rounds with every value present
+            uint32_t base0 = 0;
+            for (uint32_t q = 0; q < nfull; ++q, base0 += 32u * kG) {
+                uint32_t xb[kG];
+                const bool next_full = q + 1u < nfull;
+#pragma unroll
+                for (uint32_t g = 0; g < kG; ++g) {
+                    const uint32_t idx = base0 + 32u * (kG + g) + lane;
+                    xb[g] = (next_full || idx < len) ? __ldcs(v + idx) : 0u;
+                }
+                scan(xa, base0, true);
 #pragma unroll
                 for (uint32_t g = 0; g < kG; ++g)
                     xa[g] = xb[g];
             }
+            if (base0 < len)
+                scan(xa, base0, false);
             if (lane == 0) {
                 GapEdge e;
                 e.prefix = seen ? P : len;
