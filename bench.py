@@ -675,7 +675,7 @@ def main():
                     help="one parameter set per stream group: K distinct sets, stream s uses set "
                          "s mod K (0 = one shared set)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the serving trace (0 = skip the serving measurement)")
     ap.add_argument("--config", default="",
