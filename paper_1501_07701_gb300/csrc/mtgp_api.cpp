@@ -435,7 +435,7 @@ static void destroy_streams(mtgp_streams* h)
         if (s.ev)
             cudaEventDestroy(s.ev);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < mtgp_streams::kStages; ++b) {
         if (h->stage[b])
             cudaFree(h->stage[b]);
         if (h->ev_gen[b])
@@ -488,7 +488,7 @@ extern "C" mtgp_status mtgp_init_statuses(mtgp_params_t params, const uint32_t* 
     for (auto& sl : h->slots)
         if ((e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess)
             return bail(e, "cudaEventCreate");
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < mtgp_streams::kStages; ++b) {
         if ((e = cudaEventCreateWithFlags(&h->ev_gen[b], cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&h->ev_copy[b], cudaEventDisableTiming)) != cudaSuccess)
             return bail(e, "cudaEventCreate");
@@ -798,7 +798,7 @@ extern "C" mtgp_status mtgp_generate_to_host(mtgp_streams_t st, const uint32_t* 
     DeviceGuard g(st->device);
     cudaStream_t cs = (cudaStream_t)cuda_stream;
     if (st->stage_cap < chunk) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < mtgp_streams::kStages; ++b) {
             if (st->stage[b]) {
                 CUDA_TRY(cudaStreamSynchronize(st->copy_stream), "cudaStreamSynchronize");
                 cudaFree(st->stage[b]);
@@ -806,7 +806,7 @@ extern "C" mtgp_status mtgp_generate_to_host(mtgp_streams_t st, const uint32_t* 
             }
         }
         st->stage_cap = 0;
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < mtgp_streams::kStages; ++b)
             CUDA_TRY(cudaMalloc(&st->stage[b], chunk * 4), "cudaMalloc(staging)");
         st->stage_cap = chunk;
     }
@@ -818,11 +818,11 @@ extern "C" mtgp_status mtgp_generate_to_host(mtgp_streams_t st, const uint32_t* 
     uint64_t host_off = 0;
     uint64_t fill = 0;
     int nchunk = 0;
-    bool recorded[2] = {false, false};
+    bool recorded[mtgp_streams::kStages] = {};
     auto flush = [&]() -> mtgp_status {
         if (fill == 0)
             return MTGP_OK;
-        const int b = nchunk & 1;
+        const int b = nchunk % mtgp_streams::kStages;
         if (recorded[b])
             CUDA_TRY(cudaStreamWaitEvent(cs, st->ev_copy[b], 0), "cudaStreamWaitEvent");
         Work w;

@@ -71,10 +71,12 @@ struct mtgp_streams {
     std::tuple<int, int, int, int> geo_key{};
     mtgp::Geometry geo_cap{};
     // device-to-host path
-    void* stage[2] = {nullptr, nullptr};
+    // (kStages buffers: generation may run that many chunks ahead of the copies)
+    static constexpr int kStages = 4;
+    void* stage[kStages] = {};
     uint64_t stage_cap = 0;   // elements per staging buffer
-    cudaEvent_t ev_gen[2] = {nullptr, nullptr};
-    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    cudaEvent_t ev_gen[kStages] = {};
+    cudaEvent_t ev_copy[kStages] = {};
     cudaStream_t copy_stream = nullptr;
     // autotuning
     cudaStream_t tune_stream = nullptr;
