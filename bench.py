@@ -627,13 +627,19 @@ def measure_e2e(mtgp, torch, st, ids, counts, stream, args):
     h2d = ids.nbytes + counts.nbytes
     fmt = FORMATS[args.format]
     mtgp.mtgp_generate_to_host(st, ids, counts, fmt, host, 0, stream)   # warm-up
+    per = []
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
+        ts = time.perf_counter()
         mtgp.mtgp_generate_to_host(st, ids, counts, fmt, host, 0, stream)
+        per.append(total / (time.perf_counter() - ts) / 1e9)
     dt = time.perf_counter() - t0
+    # the device-to-host link is the bound; its rate varies with other
+    # traffic to host memory, so the per-step rates are reported as well
     return {"value": total * args.e2e_steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4 * total,
-            "steps": args.e2e_steps, "api": "mtgp_generate_to_host (pinned host output)"}
+            "steps": args.e2e_steps, "per_step_gnum_s": [round(v, 2) for v in per],
+            "api": "mtgp_generate_to_host (pinned host output)"}
 
 
 def measure_serving(mtgp, torch, args):
