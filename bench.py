@@ -547,46 +547,54 @@ def run_quality_sweep(args):
     build()
     torch.cuda.set_device(0)
     S, C, p = args.quality_sweep, args.sweep_count, args.mexp or 3217
+    SB = min(S, args.sweep_batch)   # sets per launch (bounds the output buffer)
     bounds = quality.default_hamming_bounds(1200, 4)
-    counts = np.full(S, C, np.uint64)
-    ids = np.arange(S, dtype=np.uint32)
-    seeds = np.zeros(S, np.uint32)
-    out = torch.empty(S * C, dtype=torch.int32, device="cuda")
+    out = torch.empty(SB * C, dtype=torch.int32, device="cuda")
     inside = lambda v: 1e-3 <= v <= 1.0 - 1e-3  # noqa: E731
     res = {}
     for gen in ("mtgp", "mt"):
-        if gen == "mtgp":
-            sets = [mtgp.mtgp_params_generate(p, k) for k in range(S)]
-            st = mtgp.mtgp_init_statuses_multi(sets, ids, seeds)
-        else:
-            sets = [mtgp.mtgp_mt_params_generate(p, k) for k in range(S)]
-            st = mtgp.mtgp_mt_init_multi(sets, ids, seeds)
-        torch.cuda.synchronize()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record()
-        if gen == "mtgp":
-            mtgp.mtgp_generate_u32(st, ids, counts, out)
-        else:
-            mtgp.mtgp_mt_generate(st, ids, counts, mtgp.MTGP_U32, out)
-        e1.record()
-        hist = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128)
-        tab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds)
-        e2.record()
-        torch.cuda.synchronize()
-        # bit-exact check of the first 2^16 outputs of three sets against the oracles
+        pg, ph = np.zeros(S), np.zeros(S)
+        gen_ms = stats_ms = 0.0
         exact = True
-        for k in sorted({0, S // 2, S - 1}):
+        for k0 in range(0, S, SB):
+            nb = min(SB, S - k0)
+            counts = np.full(nb, C, np.uint64)
+            ids = np.arange(nb, dtype=np.uint32)
+            seeds = np.zeros(nb, np.uint32)
             if gen == "mtgp":
-                q = oracle.params_generate(p, k)
-                ref, _ = oracle.generate(q, oracle.init_state(q, 0), min(C, 1 << 16))
+                sets = [mtgp.mtgp_params_generate(p, k0 + k) for k in range(nb)]
+                st = mtgp.mtgp_init_statuses_multi(sets, ids, seeds)
             else:
-                q = omt.params_generate(p, k)
-                ref, _ = omt.generate(q, omt.init_state(q, 0), min(C, 1 << 16))
-            got = out[k * C:k * C + ref.size].cpu().numpy().view(np.uint32)
-            exact = exact and bool(np.array_equal(got, ref))
-        pg = np.array([quality.gap_test(hist[i], b=5)["p_value"] for i in range(S)])
-        ph = np.array([quality.hamming_test(tab[i], L=1200, bounds=bounds)["p_value"]
-                       for i in range(S)])
+                sets = [mtgp.mtgp_mt_params_generate(p, k0 + k) for k in range(nb)]
+                st = mtgp.mtgp_mt_init_multi(sets, ids, seeds)
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            if gen == "mtgp":
+                mtgp.mtgp_generate_u32(st, ids, counts, out)
+            else:
+                mtgp.mtgp_mt_generate(st, ids, counts, mtgp.MTGP_U32, out)
+            e1.record()
+            hist = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128)
+            tab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds)
+            e2.record()
+            torch.cuda.synchronize()
+            gen_ms += e0.elapsed_time(e1)
+            stats_ms += e1.elapsed_time(e2)
+            # bit-exact check of the first 2^16 outputs of three sets per batch against the oracles
+            for k in sorted({0, nb // 2, nb - 1}):
+                if gen == "mtgp":
+                    q = oracle.params_generate(p, k0 + k)
+                    ref, _ = oracle.generate(q, oracle.init_state(q, 0), min(C, 1 << 16))
+                else:
+                    q = omt.params_generate(p, k0 + k)
+                    ref, _ = omt.generate(q, omt.init_state(q, 0), min(C, 1 << 16))
+                got = out[k * C:k * C + ref.size].cpu().numpy().view(np.uint32)
+                exact = exact and bool(np.array_equal(got, ref))
+            for i in range(nb):
+                pg[k0 + i] = quality.gap_test(hist[i], b=5)["p_value"]
+                ph[k0 + i] = quality.hamming_test(tab[i], L=1200, bounds=bounds)["p_value"]
+            del st
         ok_g = np.array([inside(v) for v in pg])
         ok_h = np.array([inside(v) for v in ph])
         res[gen] = {"sets": S, "pass_gap": float(ok_g.mean()), "pass_hamming": float(ok_h.mean()),
@@ -595,9 +603,8 @@ def run_quality_sweep(args):
                     "hamming_p_below_1e-3": int((ph < 1e-3).sum()),
                     "failing_gap_sets": [int(i) for i in np.nonzero(~ok_g)[0]],
                     "failing_hamming_sets": [int(i) for i in np.nonzero(~ok_h)[0]],
-                    "gen_gnum_s": S * C / (e0.elapsed_time(e1) * 1e6),
-                    "stats_ms": e1.elapsed_time(e2), "bit_exact_sample": exact}
-        del st
+                    "gen_gnum_s": S * C / (gen_ms * 1e6), "stats_ms": stats_ms,
+                    "bit_exact_sample": exact}
     print(json.dumps({"quality_sweep": {"period_exponent": p, "numbers_per_set": C,
                                         "seed_status": 0, "tests": "gap r=25 b=5 t=128; "
                                         "Hamming pairs r=25 s=5 L=1200, 4 classes",
@@ -700,6 +707,7 @@ def main():
                     help="S > 0: tests 35 and 100 over S parameter sets of MTGP and of the original "
                          "MT at period 2^mexp (default 3217), one stream each (Sec. 5.3)")
     ap.add_argument("--sweep-count", type=int, default=1 << 24, help="numbers per set in the sweep")
+    ap.add_argument("--sweep-batch", type=int, default=1000, help="sets per launch in the sweep")
     ap.add_argument("--mt-p", type=int, default=3217,
                     help="exponent of the original-MT set (19937 = MT19937, else seed-generated)")
     args = ap.parse_args()
