@@ -104,9 +104,12 @@ mtgp_status mtgp_params_generate(uint32_t mexp, uint64_t seed, mtgp_params_t* ou
 /* Sec. 3.1: parameter set from explicit fields (`desc` is copied). */
 mtgp_status mtgp_params_create(const mtgp_params_desc* desc, mtgp_params_t* out);
 
-/* Copies the completed fields (n, mask, tables filled in) into *desc. */
+/* Sec. 3.1: copies the completed fields (n, mask, tables filled in) into
+ * *desc (a host struct owned by the caller). */
 mtgp_status mtgp_params_get(mtgp_params_t params, mtgp_params_desc* desc);
 
+/* Handle bookkeeping, no counterpart in the paper: releases the handle
+ * (NULL is accepted).  Handles already copied into stream sets stay valid. */
 mtgp_status mtgp_params_free(mtgp_params_t params);
 
 /* ---------------------------------------------------------------------- */
@@ -137,17 +140,24 @@ mtgp_status mtgp_init_statuses_multi(const mtgp_params_t* sets, uint32_t n_sets,
                                      const uint32_t* set_of_stream, const uint32_t* seeds,
                                      uint32_t n_streams, void* cuda_stream, mtgp_streams_t* out);
 
-/* Overwrites all states from the host array `states` (n_streams x N words,
- * row s = stream s, oldest word first).  Synchronous. */
+/* Sec. 2 (a generator's state persists in global memory between kernel
+ * launches) and Sec. 3.1 (a user-chosen status in place of a seeded one):
+ * overwrites all device states from the host array `states` (n_streams x N
+ * words, row s = stream s, oldest word first).  Synchronous: returns after
+ * the copy.  MTGP_EINVAL for a null pointer; the masked low bits of each
+ * row's oldest word are stored as given (they never reach an output). */
 mtgp_status mtgp_set_statuses(mtgp_streams_t streams, const uint32_t* states, void* cuda_stream);
 
-/* Copies all states to the host array `states` (n_streams x N words, oldest
- * word first: after c outputs of a stream its row is x_c .. x_{c+N-1}).
- * Waits for cuda_stream.  Together with mtgp_set_statuses this is the
- * checkpoint/restore pair. */
+/* Sec. 2 (state persisting in global memory between launches): copies all
+ * states to the host array `states` (n_streams x N words, caller-owned,
+ * oldest word first: after c outputs of a stream its row is
+ * x_c .. x_{c+N-1}).  Waits for cuda_stream.  Together with
+ * mtgp_set_statuses this is the checkpoint/restore pair: restoring a saved
+ * row and generating continues the stream exactly where it was saved. */
 mtgp_status mtgp_get_statuses(mtgp_streams_t streams, uint32_t* states, void* cuda_stream);
 
-/* Number of streams and words per state. */
+/* Bookkeeping, no counterpart in the paper: number of streams and words
+ * per state (N) of the handle, into host integers (either may be NULL). */
 mtgp_status mtgp_streams_info(mtgp_streams_t streams, uint32_t* n_streams, uint32_t* n_words);
 
 /* Sec. 2 (per-block generator) and Sec. 3.2 (many statuses in one launch).
@@ -192,7 +202,12 @@ mtgp_status mtgp_generate_to_host(mtgp_streams_t streams, const uint32_t* stream
  * capture.  All calls on a device share the array and each overwrites the
  * previous contents (the claim counters are cleared on every call), so calls
  * whose kernels overlap on the GPU race: order them (one CUDA stream, one
- * host thread at a time).  Asynchronous on cuda_stream. */
+ * host thread at a time).  The work table is copied from a host array that
+ * the next call overwrites, so a call made while cuda_stream is being
+ * captured returns MTGP_EINVAL (record graphs with mtgp_plan_create).  The
+ * array's address is looked up once per device for the life of the
+ * process: a cudaDeviceReset while the library is loaded is not supported
+ * by this call.  Asynchronous on cuda_stream. */
 mtgp_status mtgp_generate_noalloc(mtgp_streams_t streams, const uint32_t* stream_ids,
                                   const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
                                   void* out, void* cuda_stream);
@@ -202,6 +217,8 @@ mtgp_status mtgp_generate_noalloc(mtgp_streams_t streams, const uint32_t* stream
  * (the word is then cleared). */
 mtgp_status mtgp_check(mtgp_streams_t streams, void* cuda_stream);
 
+/* Handle bookkeeping, no counterpart in the paper: waits for the handle's
+ * work and frees its device states (NULL is accepted). */
 mtgp_status mtgp_streams_free(mtgp_streams_t streams);
 
 /* ---------------------------------------------------------------------- */
@@ -278,7 +295,12 @@ mtgp_status mtgp_plan_set_trace(mtgp_plan_t plan, int enable);
  * 4 * n_items uint64 (n_items from mtgp_plan_get_info). */
 mtgp_status mtgp_plan_read_trace(mtgp_plan_t plan, uint64_t* host);
 
+/* Bookkeeping, no counterpart in the paper: the plan's shape and launch
+ * configuration into the caller's host struct. */
 mtgp_status mtgp_plan_get_info(mtgp_plan_t plan, mtgp_plan_info* info);
+
+/* Handle bookkeeping: waits for the plan's launches and frees its work table
+ * and graph (the streams handle is not freed). */
 mtgp_status mtgp_plan_free(mtgp_plan_t plan);
 
 /* ---------------------------------------------------------------------- */
@@ -297,6 +319,9 @@ typedef struct {
     uint64_t arena_bytes;        /* device output arena = admission cap (0 = 8 GiB) */
     uint32_t max_inflight;       /* ticks in flight at once, 1..64 (0 = 4)          */
     uint32_t max_tick_requests;  /* requests coalesced into one tick (0 = 4096)     */
+    double   tick_timeout_s;     /* longest wait for one launch's completion before
+                                    progress / run_trace return MTGP_ETIMEOUT,
+                                    seconds > 0 (0 = 60)                           */
 } mtgp_server_config;
 
 typedef struct {
@@ -315,6 +340,8 @@ typedef struct {
     uint64_t ticks;              /* kernel launches                                 */
     double   elapsed;            /* seconds from the first arrival to the last completion */
     double   busy_wait;          /* seconds the loop idled while requests were queued */
+    double   launch_host_s;      /* host seconds spent building work tables and
+                                    issuing launches (table upload + kernel)      */
 } mtgp_server_stats;
 
 /* Creates a server over `streams` (kept by reference; must outlive the
@@ -333,7 +360,10 @@ mtgp_status mtgp_server_submit(mtgp_server_t server, uint32_t stream_id, uint64_
  * one tick and launches it if a tick slot is free.  Up to `max_out`
  * completions are copied to the host array `out`; *n_out receives their
  * number (the rest stay queued for later calls).  A completion's result
- * stays valid in the arena until mtgp_server_release. */
+ * stays valid in the arena until mtgp_server_release.  MTGP_ETIMEOUT if a
+ * tick's completion has not been observed tick_timeout_s seconds after its
+ * launch (failure detection; no counterpart in the paper): nothing is lost,
+ * the tick stays in flight and a later call collects it if it completes. */
 mtgp_status mtgp_server_progress(mtgp_server_t server, mtgp_completion* out, uint32_t max_out,
                                  uint32_t* n_out);
 
@@ -349,6 +379,14 @@ mtgp_status mtgp_server_arena(mtgp_server_t server, void** arena);
 mtgp_status mtgp_server_read(mtgp_server_t server, uint64_t arena_offset, uint64_t count,
                              void* host_dst);
 
+/* Diagnostics for failure-detection tests (no counterpart in the paper):
+ * while `hold` is non-zero the server reads every launch's completion as
+ * "not ready", as if the device never reported it.  The kernels themselves
+ * run and finish normally; only the host's view is held, so
+ * mtgp_server_progress and mtgp_server_run_trace reach their MTGP_ETIMEOUT
+ * path without stalling the GPU.  hold = 0 restores normal operation. */
+mtgp_status mtgp_server_debug_hold(mtgp_server_t server, int hold);
+
 /* Replays an arrival trace in real time on an idle server: request j
  * arrives t_arrival[j] seconds after the call starts (non-decreasing) and
  * asks for counts[j] numbers of stream ids[j] in format fmts[j]; latency[j]
@@ -357,7 +395,9 @@ mtgp_status mtgp_server_read(mtgp_server_t server, uint64_t arena_offset, uint64
  * mode 1 = one launch per request on 16 CUDA streams (stream id mod 16), the
  * comparison.  If record_offsets is non-NULL it receives each result's
  * arena offset and no arena space is reused (the arena must then hold the
- * whole trace).  Synchronous. */
+ * whole trace).  Synchronous.  MTGP_ETIMEOUT as for mtgp_server_progress;
+ * the requests of the trace not yet completed then stay queued on the
+ * server (collect them with mtgp_server_progress or free the server). */
 mtgp_status mtgp_server_run_trace(mtgp_server_t server, const double* t_arrival,
                                   const uint32_t* ids, const uint64_t* counts,
                                   const int32_t* fmts, uint32_t n, uint32_t mode,

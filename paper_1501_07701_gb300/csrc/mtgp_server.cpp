@@ -8,6 +8,14 @@
 // submission order and no two kernels touch one state at once.  Requests for
 // one stream admitted into the same tick become consecutive segments of one
 // work item, in order.
+//
+// Failure detection: every wait for a tick's completion is bounded by the
+// server's tick_timeout_s.  A tick whose completion has not been observed
+// that long after its launch makes progress / run_trace return
+// MTGP_ETIMEOUT; the tick stays marked in flight, so a later call picks it up
+// if it does complete.  A diagnostic hold makes completion queries report
+// "not ready" (the kernels still run to completion), which lets tests reach
+// that path without stalling the GPU.
 #include <time.h>
 
 #include <algorithm>
@@ -99,6 +107,7 @@ struct Tick {
     cudaEvent_t ev = nullptr;
     TableSlot slot;
     bool busy = false;
+    double t_launch = 0;   // steady-clock seconds at launch
 };
 
 }  // namespace
@@ -120,7 +129,29 @@ struct mtgp_server {
     uint64_t n_numbers = 0;
     uint64_t n_requests = 0;
     bool keep_results = false;          // trace mode with recorded offsets
+    bool hold = false;                  // diagnostic: completions read as not ready
+    double launch_host_s = 0;           // host time in work-table builds and launches
 };
+
+// Completion query of one event, bounded by the server's deadline.  Returns
+// MTGP_OK with *ready set, MTGP_ETIMEOUT once `t_launch + tick_timeout_s` has
+// passed without completion, or MTGP_ECUDA for a failed query.
+static mtgp_status query_done(const mtgp_server* s, cudaEvent_t ev, double t_launch, bool* ready)
+{
+    *ready = false;
+    const cudaError_t e = s->hold ? cudaErrorNotReady : cudaEventQuery(ev);
+    if (e == cudaSuccess) {
+        *ready = true;
+        return MTGP_OK;
+    }
+    if (e != cudaErrorNotReady)
+        return fail_cuda(e, "tick completion");
+    const double waited = now_s() - t_launch;
+    if (waited > s->cfg.tick_timeout_s)
+        return fail(MTGP_ETIMEOUT, "a launch has not completed %.3f s after it was issued "
+                    "(limit %.3f s)", waited, s->cfg.tick_timeout_s);
+    return MTGP_OK;
+}
 
 static void destroy_server(mtgp_server* s)
 {
@@ -158,8 +189,12 @@ extern "C" mtgp_status mtgp_server_create(mtgp_streams_t st, const mtgp_server_c
             c.max_inflight = 4;
         if (c.max_tick_requests == 0)
             c.max_tick_requests = 4096;
+        if (c.tick_timeout_s == 0)
+            c.tick_timeout_s = 60.0;
         if (c.max_inflight > 64)
             return fail(MTGP_EINVAL, "max_inflight %u > 64", c.max_inflight);
+        if (!(c.tick_timeout_s > 0))
+            return fail(MTGP_EINVAL, "tick_timeout_s must be positive");
         DeviceGuard g(st->device);
         mtgp_server* s = new mtgp_server;
         s->st = st;
@@ -242,11 +277,12 @@ static mtgp_status reap(mtgp_server* s, int* n_reaped)
     for (Tick& t : s->ticks) {
         if (!t.busy)
             continue;
-        const cudaError_t e = cudaEventQuery(t.ev);
-        if (e == cudaErrorNotReady)
+        bool ready = false;
+        const mtgp_status qs = query_done(s, t.ev, t.t_launch, &ready);
+        if (qs != MTGP_OK)
+            return qs;
+        if (!ready)
             continue;
-        if (e != cudaSuccess)
-            return fail_cuda(e, "tick completion");
         const double tn = now_s();
         for (uint32_t i : t.reqs) {
             Req& r = s->reqs[i];
@@ -319,6 +355,7 @@ static mtgp_status admit_and_launch(mtgp_server* s, int* launched)
         return MTGP_OK;
     for (uint32_t i : t->reqs)
         s->busy[s->reqs[i].stream] = 1;
+    const double tl = now_s();
     Work w;
     mtgp_status st = build_work(s->st->n_streams, ids.data(), counts.data(), fmts.data(), 0,
                                 (uint32_t)ids.size(), 0, w, offs.data());
@@ -331,6 +368,8 @@ static mtgp_status admit_and_launch(mtgp_server* s, int* launched)
     if (e != cudaSuccess)
         return fail_cuda(e, "cudaEventRecord(tick)");
     t->busy = true;
+    t->t_launch = now_s();
+    s->launch_host_s += t->t_launch - tl;
     ++s->n_ticks;
     *launched = 1;
     return MTGP_OK;
@@ -418,6 +457,7 @@ static mtgp_status run_per_request(mtgp_server* s, const double* t_arr, const ui
     std::vector<TableSlot> slots(NS);
     std::vector<cudaEvent_t> evs(NS, nullptr);
     std::vector<int64_t> slot_req(NS, -1);
+    std::vector<double> slot_t(NS, 0.0);
     mtgp_status rc = MTGP_OK;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < L && e == cudaSuccess; ++i)
@@ -443,13 +483,11 @@ static mtgp_status run_per_request(mtgp_server* s, const double* t_arr, const ui
         for (size_t k = 0; k < NS && in_flight; ++k) {
             if (slot_req[k] < 0)
                 continue;
-            e = cudaEventQuery(evs[k]);
-            if (e == cudaErrorNotReady)
-                continue;
-            if (e != cudaSuccess) {
-                rc = fail_cuda(e, "per-request completion");
+            bool ready = false;
+            if ((rc = query_done(s, evs[k], slot_t[k], &ready)) != MTGP_OK)
                 break;
-            }
+            if (!ready)
+                continue;
             const uint32_t j = (uint32_t)slot_req[k];
             latency[j] = now_s() - t0 - t_arr[j];
             if (!rec_offs)
@@ -470,6 +508,7 @@ static mtgp_status run_per_request(mtgp_server* s, const double* t_arr, const ui
             offs[j] = off;
             if (rec_offs)
                 rec_offs[j] = off;
+            const double tl = now_s();
             Work w;
             rc = build_work(s->st->n_streams, &ids[j], &counts[j], &fmts[j], 0, 1, 0, w, &off);
             if (rc != MTGP_OK)
@@ -483,6 +522,8 @@ static mtgp_status run_per_request(mtgp_server* s, const double* t_arr, const ui
                 break;
             }
             slot_req[slot_next] = j;
+            slot_t[slot_next] = now_s();
+            s->launch_host_s += slot_t[slot_next] - tl;
             slot_next = (slot_next + 1) % NS;
             ++in_flight;
             ++s->n_ticks;
@@ -532,6 +573,7 @@ extern "C" mtgp_status mtgp_server_run_trace(mtgp_server_t s, const double* t_ar
             if (t.busy)
                 return fail(MTGP_EBUSY, "server has ticks in flight");
         const uint64_t ticks0 = s->n_ticks, nums0 = s->n_numbers, reqs0 = s->n_requests;
+        const double launch0 = s->launch_host_s;
         double busy_wait = 0;
         const double t0 = now_s();
         mtgp_status rc = MTGP_OK;
@@ -582,6 +624,7 @@ extern "C" mtgp_status mtgp_server_run_trace(mtgp_server_t s, const double* t_ar
             stats->ticks = s->n_ticks - ticks0;
             stats->elapsed = t1 - t0 - (n ? t_arrival[0] : 0);
             stats->busy_wait = busy_wait;
+            stats->launch_host_s = s->launch_host_s - launch0;
         }
         if (rc != MTGP_OK)
             return rc;
@@ -589,6 +632,14 @@ extern "C" mtgp_status mtgp_server_run_trace(mtgp_server_t s, const double* t_ar
     } catch (...) {
         return fail(MTGP_ENOMEM, "host allocation failed");
     }
+}
+
+extern "C" mtgp_status mtgp_server_debug_hold(mtgp_server_t s, int hold)
+{
+    if (!s)
+        return fail(MTGP_EINVAL, "null server");
+    s->hold = hold != 0;
+    return ok();
 }
 
 extern "C" mtgp_status mtgp_server_free(mtgp_server_t s)

@@ -64,7 +64,7 @@ class MtParams(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
-                ("max_tick_requests", ctypes.c_uint32)]
+                ("max_tick_requests", ctypes.c_uint32), ("tick_timeout_s", ctypes.c_double)]
 
 
 class Completion(ctypes.Structure):
@@ -76,7 +76,7 @@ class Completion(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_uint64), ("numbers", ctypes.c_uint64),
                 ("ticks", ctypes.c_uint64), ("elapsed", ctypes.c_double),
-                ("busy_wait", ctypes.c_double)]
+                ("busy_wait", ctypes.c_double), ("launch_host_s", ctypes.c_double)]
 
 
 _VP = ctypes.c_void_p
@@ -131,6 +131,7 @@ _SIGS = {
     "mtgp_server_run_trace": [_VP, ctypes.POINTER(ctypes.c_double), _U32P, _U64P,
                               ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_uint32,
                               ctypes.POINTER(ctypes.c_double), _U64P, ctypes.POINTER(ServerStats)],
+    "mtgp_server_debug_hold": [_VP, ctypes.c_int],
     "mtgp_server_free": [_VP],
     "mtgp_mt_params_mt19937": [ctypes.POINTER(MtParams)],
     "mtgp_mt_params_generate": [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(MtParams)],
@@ -478,8 +479,9 @@ class Server:
             pass
 
 
-def mtgp_server_create(streams: Streams, arena_bytes=0, max_inflight=0, max_tick_requests=0):
-    c = ServerConfig(arena_bytes, max_inflight, max_tick_requests)
+def mtgp_server_create(streams: Streams, arena_bytes=0, max_inflight=0, max_tick_requests=0,
+                       tick_timeout_s=0.0):
+    c = ServerConfig(arena_bytes, max_inflight, max_tick_requests, tick_timeout_s)
     h = _VP()
     _call("mtgp_server_create", streams.handle, ctypes.byref(c), ctypes.byref(h))
     return Server(h, streams)
@@ -496,6 +498,10 @@ def mtgp_server_progress(server: Server, max_out=1024):
     _call("mtgp_server_progress", server.handle, buf, max_out, ctypes.byref(n))
     return [{"tag": c.tag, "count": c.count, "arena_offset": c.arena_offset, "fmt": c.fmt,
              "submit_time": c.submit_time, "done_time": c.done_time} for c in buf[:n.value]]
+
+
+def mtgp_server_debug_hold(server: Server, hold: bool = True):
+    _call("mtgp_server_debug_hold", server.handle, int(bool(hold)))
 
 
 def mtgp_server_release(server: Server, arena_offset, count):
@@ -533,7 +539,8 @@ def mtgp_server_run_trace(server: Server, t_arrival, ids, counts, fmts, mode=0, 
           lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
           _p64(offs) if record else None, ctypes.byref(st))
     return lat, offs, {"requests": st.requests, "numbers": st.numbers, "ticks": st.ticks,
-                       "elapsed": st.elapsed, "busy_wait": st.busy_wait}
+                       "elapsed": st.elapsed, "busy_wait": st.busy_wait,
+                       "launch_host_s": st.launch_host_s}
 
 
 # ---------------------------------------------------------------------------

@@ -109,3 +109,88 @@ def test_submit_rejects_oversized_and_bad_ids():
     with pytest.raises(mtgp.MtgpError) as ei:
         mtgp.mtgp_server_submit(srv, 9, 10, 0, 1)
     assert ei.value.status == 1
+
+
+def test_progress_times_out_when_completion_is_not_seen():
+    """Failure detection on the host: with the diagnostic hold the server
+    never sees its tick complete (the kernel itself runs normally), so
+    progress must give up with MTGP_ETIMEOUT once tick_timeout_s has passed,
+    keep the tick, and deliver the exact result once the hold is lifted."""
+    import time
+    st, op, states0 = _setup(4)
+    srv = mtgp.mtgp_server_create(st, arena_bytes=4 << 20, tick_timeout_s=0.2)
+    mtgp.mtgp_server_debug_hold(srv, True)
+    mtgp.mtgp_server_submit(srv, 2, 5000, mtgp.MTGP_U32, 77)
+    t0 = time.monotonic()
+    with pytest.raises(mtgp.MtgpError) as ei:
+        while time.monotonic() - t0 < 5.0:
+            assert mtgp.mtgp_server_progress(srv) == []
+            time.sleep(0.01)
+    assert ei.value.status == 4                      # MTGP_ETIMEOUT
+    assert 0.2 <= time.monotonic() - t0 < 5.0
+    mtgp.mtgp_server_debug_hold(srv, False)
+    got = []
+    while not got:
+        got = mtgp.mtgp_server_progress(srv)
+    assert got[0]["tag"] == 77
+    ref, _ = oracle.generate(op, states0[2], 5000)
+    assert np.array_equal(mtgp.mtgp_server_read(srv, got[0]["arena_offset"], 5000), ref)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_run_trace_times_out_when_completion_is_not_seen(mode):
+    """Both replay modes return MTGP_ETIMEOUT instead of waiting forever when
+    completions are never observed; freeing the server afterwards waits for
+    the (finished) kernels and returns normally."""
+    st, _, _ = _setup(8)
+    srv = mtgp.mtgp_server_create(st, arena_bytes=16 << 20, tick_timeout_s=0.1)
+    mtgp.mtgp_server_debug_hold(srv, True)
+    t = np.array([0.0, 0.001, 0.002])
+    with pytest.raises(mtgp.MtgpError) as ei:
+        mtgp.mtgp_server_run_trace(srv, t, np.array([1, 2, 1], np.uint32),
+                                   np.array([1000, 2000, 3000], np.uint64),
+                                   np.zeros(3, np.int32), mode=mode)
+    assert ei.value.status == 4
+    srv.close()
+
+
+def test_serving_trace_prefix_at_full_size():
+    """The serving workload itself (65 536 resident streams, the seed-11
+    Poisson arrivals at 50 000 requests/s, k log-uniform in [2^8, 2^20], u32
+    or f32 [0,1), 8 GiB admission arena), replayed in real time through
+    continuous batching for the prefix of the trace whose outputs fit the
+    arena at once (about 0.2 s of arrivals).  Every request's output must
+    equal the oracle's replay of that stream's requests alone and in order,
+    and every final state must match."""
+    from concurrent.futures import ThreadPoolExecutor
+    tr = workloads.serving_trace()                        # the 10 s trace; its prefix
+    cum = np.cumsum(tr["counts"].astype(np.int64))
+    n = int(np.searchsorted(cum, 1_200_000_000))          # ~4.8 GB of results
+    t, ids, counts, fmts = tr["t"][:n], tr["ids"][:n], tr["counts"][:n], tr["fmt"][:n]
+    st, op, states0 = _setup(tr["n_streams"])
+    srv = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4)
+    lat, offs, stats = mtgp.mtgp_server_run_trace(srv, t, ids, counts, fmts, mode=0, record=True)
+    assert stats["requests"] == n and stats["ticks"] < n
+    end = int((offs + counts).max())
+    arena = mtgp.mtgp_server_read(srv, 0, end)
+    per_stream = {}
+    for j in range(n):
+        per_stream.setdefault(int(ids[j]), []).append(j)
+
+    def replay(sid):
+        s = states0[sid].copy()
+        for j in per_stream[sid]:
+            ref, s = oracle.generate(op, s, int(counts[j]), int(fmts[j]))
+            got = arena[int(offs[j]):int(offs[j]) + int(counts[j])]
+            if not np.array_equal(got, ref):
+                return "request %d (stream %d) differs" % (j, sid), s
+        return None, s
+
+    final = states0.copy()
+    with ThreadPoolExecutor(THREADS) as ex:
+        for sid, (err, s) in zip(per_stream, ex.map(replay, list(per_stream))):
+            assert err is None, err
+            final[sid] = s
+    assert np.array_equal(mtgp.mtgp_get_statuses(st), final)
+    print("serving prefix verified: %d requests, %.3f s of arrivals, %d numbers" % (
+        n, float(t[-1]), int(counts.sum())))
