@@ -16,6 +16,14 @@
 // device: a call overwrites what the previous one left there, and two calls
 // whose kernels overlap on the GPU (different CUDA streams, or different
 // host threads) race on it.  Callers must order such calls themselves.
+//
+// The work table is copied from one static host array that the next call
+// overwrites, so a call is refused while its CUDA stream is being captured
+// (a captured copy would read that array when the graph is replayed, long
+// after the call that filled it).  The device address of the scratch array
+// is looked up once per device and kept for the life of the process; a
+// device reset (cudaDeviceReset) while the library is loaded is therefore not
+// supported by this call.
 #include <cstring>
 #include <mutex>
 
@@ -77,6 +85,7 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
                                              const uint64_t* counts, uint32_t n_req, mtgp_format fmt,
                                              void* out, void* cuda_stream)
 {
+    GUARD_BEGIN
     if (!st)
         return fail(MTGP_EINVAL, "null handle");
     if ((uint32_t)fmt > 2)
@@ -103,8 +112,17 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
         return fail(MTGP_EINVAL, "null output pointer");
 
     DeviceGuard guard(st->device);
+    cudaStream_t cs = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(cs, &capturing);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "cudaStreamIsCapturing");
+    if (capturing != cudaStreamCaptureStatusNone)
+        return fail(MTGP_EINVAL, "mtgp_generate_noalloc cannot be recorded into a CUDA graph: its "
+                                 "work table is copied from host memory that the next call "
+                                 "overwrites (use mtgp_plan_create for graphs)");
     void* scratch = nullptr;
-    cudaError_t e = scratch_address(st->device, &scratch);
+    e = scratch_address(st->device, &scratch);
     if (e != cudaSuccess)
         return fail_cuda(e, "cudaGetSymbolAddress(no-alloc scratch)");
 
@@ -177,7 +195,6 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
     // returns) and launch.  The counters are part of the upload, so every
     // call starts them at zero.
     const size_t bytes = kCountersBytes + kItemsBytes + (size_t)n_segs * sizeof(Segment);
-    cudaStream_t cs = (cudaStream_t)cuda_stream;
     e = cudaMemcpyAsync(scratch, T.bytes, bytes, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess)
         return fail_cuda(e, "cudaMemcpyAsync(no-alloc table)");
@@ -199,4 +216,5 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
     if (e != cudaSuccess)
         return fail_cuda(e, "generation kernel launch (no-alloc)");
     return ok();
+    GUARD_END
 }

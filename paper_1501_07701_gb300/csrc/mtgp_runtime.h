@@ -3,6 +3,7 @@
 #pragma once
 
 #include <array>
+#include <new>
 #include <tuple>
 #include <vector>
 
@@ -50,6 +51,14 @@ mtgp_status fail_cuda(cudaError_t e, const char* what);
 mtgp_status ok();
 
 }  // namespace mtgp
+
+// Keeps C++ exceptions from crossing the C ABI: an entry point's body sits
+// between GUARD_BEGIN and GUARD_END and returns a status instead.
+#define GUARD_BEGIN try {
+#define GUARD_END                                                                      \
+    }                                                                                  \
+    catch (const std::bad_alloc&) { return fail(MTGP_ENOMEM, "host allocation failed"); } \
+    catch (...) { return fail(MTGP_EINVAL, "unexpected internal error"); }
 
 struct mtgp_streams {
     mtgp_params P;
