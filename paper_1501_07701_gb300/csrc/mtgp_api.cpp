@@ -47,11 +47,13 @@ mtgp_status mtgp::ok()
     return MTGP_OK;
 }
 
-#define GUARD_BEGIN try {
-#define GUARD_END                                                                      \
-    }                                                                                  \
-    catch (const std::bad_alloc&) { return fail(MTGP_ENOMEM, "host allocation failed"); } \
-    catch (...) { return fail(MTGP_EINVAL, "unexpected internal error"); }
+// Prefixes the last error message with the tuning candidate that produced it.
+static mtgp_status fail_candidate(mtgp_status r, const LaunchCfg& c)
+{
+    const std::string why = g_last_error;
+    return fail(r, "tuning candidate (warps/CTA %d, sub-steps %d, CTAs/SM %d, kernel %d, coop %d%%): %s",
+                c.warps_per_cta, c.k, c.ctas_per_sm, c.kernel, c.coop_percent, why.c_str());
+}
 
 #define CUDA_TRY(call, what)                   \
     do {                                       \
@@ -1092,10 +1094,15 @@ extern "C" mtgp_status mtgp_autotune(mtgp_streams_t st, mtgp_format fmt, uint32_
         float best_ms = 1e30f;
         if (r == MTGP_OK) {
             for (const LaunchCfg& c : tuning_candidates(st->P.k)) {
+                Geometry probe;
+                if (geometry_for(st, c, 1, &probe) != MTGP_OK)
+                    continue;   // not launchable on this device (registers or shared memory)
                 float ms = 0;
                 r = time_config(st, w, c, scratch, out, 2, &ms);
-                if (r != MTGP_OK)
+                if (r != MTGP_OK) {
+                    r = fail_candidate(r, c);
                     break;
+                }
                 if (ms < best_ms) {
                     best_ms = ms;
                     win = c;
@@ -1275,10 +1282,15 @@ extern "C" mtgp_status mtgp_plan_autotune(mtgp_plan_t p, mtgp_launch_config* bes
     float best_ms = 1e30f;
     if (r == MTGP_OK) {
         for (const LaunchCfg& c : tuning_candidates(st->P.k)) {
+            Geometry probe;
+            if (geometry_for(st, c, 1, &probe) != MTGP_OK)
+                continue;   // not launchable on this device (registers or shared memory)
             float ms = 0;
             r = time_config(st, p->work, c, scratch, p->out, 2, &ms);
-            if (r != MTGP_OK)
+            if (r != MTGP_OK) {
+                r = fail_candidate(r, c);
                 break;
+            }
             if (ms < best_ms) {
                 best_ms = ms;
                 win = c;
