@@ -119,6 +119,51 @@ def oracle_params_of(w):
     return get
 
 
+def rank_workload(args, rank: int, world: int):
+    """This rank's share of the job.  weak: its own instance of the workload
+    (stream seeds shifted by rank), so per-GPU work is fixed as ranks are
+    added; strong: the contiguous range of one instance's streams that
+    dist.strong_range gives this rank, so the job's work is fixed."""
+    if getattr(args, "split", "weak") == "strong" and world > 1:
+        w, desc = workload(args.workload, 0, args.streams, args.count, args.param_sets,
+                           mexp=args.mexp)
+        a, b = mdist.strong_range(w["seeds"].size, rank, world)
+        w = dict(w, seeds=w["seeds"][a:b], counts=w["counts"][a:b],
+                 param_seeds=None if w["param_seeds"] is None else w["param_seeds"][a:b])
+        desc += "; split into %d contiguous stream ranges, one per GPU" % world
+        return w, desc
+    return workload(args.workload, rank, args.streams, args.count, args.param_sets, mexp=args.mexp)
+
+
+class bracket:
+    """Barrier + device synchronisation on entry and on exit of the timed
+    region, so every rank starts and ends it together."""
+
+    def __init__(self, dist, sync):
+        self.dist, self.sync = dist, sync
+
+    def __enter__(self):
+        if self.dist:
+            self.dist.barrier()
+        self.sync()
+        return self
+
+    def __exit__(self, *exc):
+        self.sync()
+        if self.dist:
+            self.dist.barrier()
+        return False
+
+
+def job_rate(local_numbers: int, local_elapsed: float, device=None):
+    """Whole-job throughput over all ranks: the numbers every rank produced
+    divided by the slowest rank's elapsed time.  Returns (Gnumbers/s,
+    elapsed max over ranks, numbers summed over ranks)."""
+    elapsed = mdist.max_over_ranks(local_elapsed, device=device)
+    numbers = mdist.sum_over_ranks(float(local_numbers), device=device)
+    return numbers / elapsed / 1e9, elapsed, numbers
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
 
@@ -252,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w, desc = workload(args.workload, rank, args.streams, args.count, args.param_sets, mexp=args.mexp)
+    w, desc = rank_workload(args, rank, world)
     counts = w["counts"]
     total = int(counts.sum())
     stream = torch.cuda.Stream()
@@ -295,31 +340,22 @@ def run_ours(args, rank, world, local_rank):
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = cvd.split(",")[local_rank] if cvd else str(local_rank)
     clocks = ClockSampler(smi_index)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)   # let the sampler start
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            mtgp.mtgp_plan_launch(plan, stream)
-            ev[i][1].record(stream)
-            flush.fill_(i)
-    t1.record(stream)
-    stream.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    with bracket(dist, torch.cuda.synchronize):
+        t0.record(stream)
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                ev[i][0].record(stream)
+                mtgp.mtgp_plan_launch(plan, stream)
+                ev[i][1].record(stream)
+                flush.fill_(i)
+        t1.record(stream)
     clk = clocks.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
     kern_ms = [a.elapsed_time(b) for a, b in ev]
-    elapsed = mdist.max_over_ranks(elapsed, device=dev)
-    numbers_all = total * args.steps * world
-    value = numbers_all / elapsed / 1e9
+    value, elapsed, _ = job_rate(total * args.steps, t0.elapsed_time(t1) / 1e3, device=dev)
 
     # roofline of the dominant kernel (the persistent generation kernel)
     peak, peak_src = hbm_peak()
@@ -351,9 +387,18 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         e2e = measure_e2e(mtgp, torch, st, ids, counts, stream, args)
 
+    per_stream = None
+    if rank == 0 and args.workload == "uneven" and not args.no_extra:
+        per_stream = measure_per_stream_launches(mtgp, torch, st, w, out, stream, flush)
+
+    configs = None
+    if rank == 0 and not args.no_extra:
+        del plan
+        configs = measure_configs(mtgp, torch, dev, stream, flush)
+
     serving = None
     if rank == 0 and args.serving_seconds > 0:
-        del plan
+        plan = None
         serving = measure_serving(mtgp, torch, args)
 
     cpu = None
@@ -367,10 +412,12 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong" if args.split == "strong" else "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": desc, "numbers_per_step_per_gpu": total, "format": args.format,
-                       "parallelism": "independent streams per GPU" if world > 1 else "1 GPU",
+                       "parallelism": ("1 GPU" if world == 1 else
+                                       "one contiguous stream range per GPU" if args.split == "strong"
+                                       else "independent streams per GPU"),
                        "l2": "20 GB written per step (> 129 MB L2) plus a 256 MiB rewrite "
                              "between timed steps",
                        "launch": info["config"], "grid_ctas": info["grid_ctas"],
@@ -389,6 +436,8 @@ def run_ours(args, rank, world, local_rank):
             "e2e": e2e,
             "gpu_launches": args.steps * info["kernel_launches"],
             "bit_exact_sample": bit_exact,
+            "one_launch_per_stream": per_stream,
+            "configs": configs,
             "serving": serving,
             "quality": qual,
             "cpu_baseline": cpu,
@@ -649,27 +698,178 @@ def measure_e2e(mtgp, torch, st, ids, counts, stream, args):
             "api": "mtgp_generate_to_host (pinned host output)"}
 
 
-def measure_serving(mtgp, torch, args):
-    """Continuous batching vs one launch per request on the serving trace."""
-    tr = workloads.serving_trace(duration_s=args.serving_seconds)
+def measure_per_stream_launches(mtgp, torch, st, w, out, stream, flush):
+    """The uneven workload without batching: one mtgp_generate_u32 call per
+    stream, in stream order on one CUDA stream (each call uploads a
+    one-stream work table and launches one kernel), timed with CUDA events
+    over the whole sequence; whole outputs of a few streams are checked
+    against the oracle."""
+    counts = w["counts"]
+    n = counts.size
+    offs = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
+    states0 = mtgp.mtgp_get_statuses(st, stream)
+    flush.fill_(3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_host = time.perf_counter()
+    e0.record(stream)
+    for i in range(n):
+        mtgp.mtgp_generate_u32(st, np.array([i], np.uint32), counts[i:i + 1],
+                               out[int(offs[i]):int(offs[i + 1])], stream)
+    e1.record(stream)
+    stream.synchronize()
+    t_host = time.perf_counter() - t_host
+    sec = e0.elapsed_time(e1) / 1e3
+    mtgp.mtgp_check(st, stream)
+    exact = spot_check(w, counts, out, states0, 0)
+    total = int(counts.sum())
+    return {"launches": n, "gnum_s": total / sec / 1e9, "ms": 1e3 * sec,
+            "host_s": t_host, "bit_exact_sample": exact,
+            "how": "mtgp_generate_u32 once per stream, stream order, one CUDA stream"}
+
+
+# (label, workload, format) of the other configurations measured beside the
+# uneven headline: 4096 x 2^18 at Mexp 11213, and 1024 x 2^20 at Mexp 23209
+# and 44497 in the three output formats.
+EXTRA_CONFIGS = [("equal 4096 x 2^18, Mexp 11213, u32", "equal", "u32")] + [
+    ("long 1024 x 2^20, Mexp %d, %s" % (m, f), "long%d" % m, f)
+    for m in (23209, 44497) for f in ("u32", "f12", "f01")]
+
+
+def measure_configs(mtgp, torch, dev, stream, flush, steps=5, warmup=3):
+    """Each configuration as the headline is measured: an autotuned plan
+    (one persistent graph-replayed launch), L2 rewritten between launches,
+    CUDA events around each launch; the first launch's whole outputs of the
+    first, middle and last streams are checked against the oracle."""
+    peak, _ = hbm_peak()
+    res = []
+    buf = None
+    for label, name, fmt_name in EXTRA_CONFIGS:
+        w, desc = workload(name, 0)
+        counts = w["counts"]
+        total = int(counts.sum())
+        if buf is None or buf.numel() < total:
+            buf = torch.empty(total, dtype=torch.int32, device=dev)
+        out = buf[:total]
+        fmt = FORMATS[fmt_name]
+        params = mtgp.mtgp_params_generate(w["mexp"], workloads.PARAM_SEED)
+        st = mtgp.mtgp_init_statuses(params, w["seeds"], stream)
+        ids = np.arange(counts.size, dtype=np.uint32)
+        plan = mtgp.mtgp_plan_create(st, ids, counts, fmt, out)
+        mtgp.mtgp_plan_autotune(plan)
+        info = mtgp.mtgp_plan_get_info(plan)
+        states0 = mtgp.mtgp_get_statuses(st, stream)
+        exact = None
+        with torch.cuda.stream(stream):
+            for i in range(warmup):
+                mtgp.mtgp_plan_launch(plan, stream)
+                if i == 0:
+                    stream.synchronize()
+                    exact = spot_check(w, counts, out, states0, fmt)
+                flush.fill_(i)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                ev[i][0].record(stream)
+                mtgp.mtgp_plan_launch(plan, stream)
+                ev[i][1].record(stream)
+                flush.fill_(i)
+        t1.record(stream)
+        stream.synchronize()
+        mtgp.mtgp_check(st, stream)
+        kern = sum(a.elapsed_time(b) for a, b in ev) / steps / 1e3
+        n_words = mtgp.mtgp_streams_info(st)[1]
+        alg = 4.0 * total + 8.0 * n_words * counts.size
+        res.append({"config": label, "workload": desc, "format": fmt_name, "numbers": total,
+                    "gnum_s": total * steps / (t0.elapsed_time(t1) / 1e3) / 1e9,
+                    "kernel_ms_avg": 1e3 * kern, "frac": alg / kern / 1e9 / peak,
+                    "launch": info["config"], "bit_exact_sample": exact})
+        del plan, st
+    return res
+
+
+def verify_serving_prefix(mtgp, tr, n_streams, budget=1_200_000_000):
+    """Replays the prefix of the serving trace whose results fit the 8 GiB
+    arena at once, through continuous batching, recording every result's
+    arena offset; then checks every request of the prefix against the
+    oracle's replay of its stream's requests alone and in order, and every
+    final state."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cum = np.cumsum(tr["counts"].astype(np.int64))
+    n = int(np.searchsorted(cum, budget))
+    t, ids, counts, fmts = tr["t"][:n], tr["ids"][:n], tr["counts"][:n], tr["fmt"][:n]
     params = mtgp.mtgp_params_generate(workloads.MEXP_MAIN, workloads.PARAM_SEED)
-    st = mtgp.mtgp_init_statuses(params, np.arange(tr["n_streams"], dtype=np.uint32))
+    st = mtgp.mtgp_init_statuses(params, np.arange(n_streams, dtype=np.uint32))
+    states0 = mtgp.mtgp_get_statuses(st)
     srv = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4)
-    res = {"workload": "65536 resident Mexp 11213 streams; Poisson %.0f req/s (seed 11) for %.1f s; "
-                       "k = floor(2^U), U~U[8,20]; u32 or f32[0,1); arena (admission cap) 8 GiB"
-                       % (50000, args.serving_seconds),
-           "requests": int(tr["t"].size),
-           "offered_gnum_s": float(tr["counts"].sum()) / args.serving_seconds / 1e9}
-    for mode, name in [(0, "continuous_batching"), (1, "one_launch_per_request")]:
-        lat, _, stats = mtgp.mtgp_server_run_trace(srv, tr["t"], tr["ids"], tr["counts"], tr["fmt"],
-                                                   mode=mode)
-        res[name] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                     "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                     "mean_ms": 1e3 * float(lat.mean()),
-                     "gnum_s": stats["numbers"] / stats["elapsed"] / 1e9,
-                     "kernel_launches": int(stats["ticks"]), "elapsed_s": stats["elapsed"]}
+    _, offs, _ = mtgp.mtgp_server_run_trace(srv, t, ids, counts, fmts, mode=0, record=True)
+    arena = mtgp.mtgp_server_read(srv, 0, int((offs + counts).max()))
+    op = oracle.params_generate(workloads.MEXP_MAIN, workloads.PARAM_SEED)
+    per = {}
+    for j in range(n):
+        per.setdefault(int(ids[j]), []).append(j)
+
+    def replay(sid):
+        s = states0[sid].copy()
+        good = True
+        for j in per[sid]:
+            ref, s = oracle.generate(op, s, int(counts[j]), int(fmts[j]))
+            good = good and bool(np.array_equal(arena[int(offs[j]):int(offs[j]) + int(counts[j])],
+                                                ref))
+        return good, s
+
+    final = states0.copy()
+    ok = True
+    with ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+        for sid, (good, s) in zip(per, ex.map(replay, list(per))):
+            ok = ok and good
+            final[sid] = s
+    ok = ok and bool(np.array_equal(mtgp.mtgp_get_statuses(st), final))
     srv.close()
     st.close()
+    return {"requests": n, "arrivals_s": float(t[-1]), "numbers": int(counts.sum()),
+            "bit_exact": ok}
+
+
+def measure_serving(mtgp, torch, args):
+    """Continuous batching vs one launch per request: on the serving trace
+    (50 000 requests/s, which overloads the one-launch-per-request arm), and
+    on a trace at a rate that arm sustains (its latencies are then service
+    times, not backlog).  Each arm's host time per launch (work-table build,
+    upload and kernel launch) is reported beside its latencies."""
+    rate_lo, secs_lo = 20000.0, min(5.0, args.serving_seconds)
+    traces = [("offered_50k_req_s", workloads.serving_trace(duration_s=args.serving_seconds),
+               50000.0, args.serving_seconds),
+              ("sustained_20k_req_s", workloads.serving_trace(duration_s=secs_lo, rate=rate_lo),
+               rate_lo, secs_lo)]
+    n_streams = traces[0][1]["n_streams"]
+    params = mtgp.mtgp_params_generate(workloads.MEXP_MAIN, workloads.PARAM_SEED)
+    st = mtgp.mtgp_init_statuses(params, np.arange(n_streams, dtype=np.uint32))
+    srv = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4)
+    res = {"workload": "65536 resident Mexp 11213 streams; Poisson arrivals (seed 11); "
+                       "k = floor(2^U), U~U[8,20]; u32 or f32[0,1); arena (admission cap) 8 GiB"}
+    for key, tr, rate, secs in traces:
+        r = {"rate_req_s": rate, "seconds": secs, "requests": int(tr["t"].size),
+             "offered_gnum_s": float(tr["counts"].sum()) / secs / 1e9}
+        for mode, name in [(0, "continuous_batching"), (1, "one_launch_per_request")]:
+            lat, _, stats = mtgp.mtgp_server_run_trace(srv, tr["t"], tr["ids"], tr["counts"],
+                                                       tr["fmt"], mode=mode)
+            r[name] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                       "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                       "mean_ms": 1e3 * float(lat.mean()),
+                       "gnum_s": stats["numbers"] / stats["elapsed"] / 1e9,
+                       "kernel_launches": int(stats["ticks"]), "elapsed_s": stats["elapsed"],
+                       "host_us_per_launch": 1e6 * stats["launch_host_s"] / max(1, stats["ticks"])}
+        res[key] = r
+    srv.close()
+    st.close()
+    if not args.no_serving_parity:
+        res["parity_prefix"] = verify_serving_prefix(mtgp, traces[0][1], n_streams)
     return res
 
 
@@ -699,6 +899,13 @@ def main():
     ap.add_argument("--no-quality", dest="quality", action="store_false",
                     help="skip the gap and Hamming-weight statistics over the generated output")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the equal/long workloads and the one-launch-per-stream comparison")
+    ap.add_argument("--no-serving-parity", action="store_true",
+                    help="skip the oracle replay of the serving trace's prefix")
+    ap.add_argument("--split", default="weak", choices=["weak", "strong"],
+                    help="N > 1: weak = one workload instance per GPU; strong = one instance cut "
+                         "into contiguous stream ranges")
     ap.add_argument("--mexp", type=int, default=0,
                     help="MTGP exponent of the workload (0 = the workload's own, 11213 for uneven)")
     ap.add_argument("--generator", default="mtgp", choices=["mtgp", "mt"],

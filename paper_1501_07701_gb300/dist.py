@@ -7,7 +7,8 @@ its own outputs.  Two splits are used:
 * weak scaling (the benchmark): each rank runs its own instance of a
   workload, its stream seeds offset by rank * n_streams, so per-GPU work is
   fixed as ranks are added;
-* strong scaling: one set of streams is cut into contiguous ranges.
+* strong scaling: one set of streams is cut into contiguous ranges, one per
+  rank, so the job's total work is fixed as ranks are added.
 
 The only collectives are host-side bookkeeping (barrier, max of elapsed
 times); none touches generated data.
@@ -30,6 +31,17 @@ def strong_range(n_streams: int, rank: int, world: int):
     start = rank * base + min(rank, extra)
     stop = start + base + (1 if rank < extra else 0)
     return start, stop
+
+
+def sum_over_ranks(value: float, device=None) -> float:
+    """Sum of a float over the default process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
 def max_over_ranks(value: float, device=None) -> float:

@@ -91,3 +91,58 @@ def test_strong_ranges_partition():
             assert rs[0][0] == 0 and rs[-1][1] == n
             for (a, b), (c, d) in zip(rs, rs[1:]):
                 assert b == c and b >= a
+
+
+def _bench_worker(rank, world, port, split, q):
+    """One rank of bench.py's own multi-rank control path on gloo: the shard
+    this rank would run, the barrier-bracketed timed region and the
+    whole-job rate (numbers summed over ranks / slowest rank's time)."""
+    import argparse
+    import time
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        args = argparse.Namespace(workload="uneven", streams=0, count=0, param_sets=0, mexp=0,
+                                  split=split)
+        w, desc = bench.rank_workload(args, rank, world)
+        syncs = []
+        with bench.bracket(dist, lambda: syncs.append(time.monotonic())):
+            t_local = 0.5 + rank          # rank 1 is the slowest
+        value, elapsed, numbers = bench.job_rate(int(w["counts"].sum()), t_local)
+        shards = [None] * world
+        dist.all_gather_object(shards, (w["seeds"].tolist(), w["counts"].tolist(), desc))
+        if rank == 0:
+            q.put((shards, value, elapsed, numbers, len(syncs)))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("split", ["weak", "strong"])
+def test_bench_control_path_two_ranks(split):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_worker, args=(r, 2, port, split, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    shards, value, elapsed, numbers, n_sync = q.get(timeout=120)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    full = workloads.uneven()
+    (s0, c0, d0), (s1, c1, d1) = shards
+    if split == "strong":
+        # one instance cut into two contiguous ranges that cover it exactly
+        assert s0 + s1 == full["seeds"].tolist() and c0 + c1 == full["counts"].tolist()
+        assert abs(len(s0) - len(s1)) <= 1 and "contiguous" in d0
+        assert numbers == float(full["counts"].sum())
+    else:
+        # two instances of the whole workload with disjoint stream seeds
+        assert c0 == c1 == full["counts"].tolist() and not set(s0) & set(s1)
+        assert numbers == 2.0 * float(full["counts"].sum())
+    assert elapsed == 1.5 and n_sync == 2
+    assert value == pytest.approx(numbers / 1.5 / 1e9)
