@@ -41,10 +41,8 @@ UNIT = "Gnumbers/s"
 # used only while these still hash to the value it was taken on)
 KERNEL_SOURCES = {
     "mtgp_fast_kernel": ["paper_1501_07701_gb300/csrc/mtgp_fast.cuh"],
-    "mtgp_wide_kernel": ["paper_1501_07701_gb300/csrc/mtgp_fast.cuh",
-                         "paper_1501_07701_gb300/csrc/mtgp_wide.cuh"],
 }
-KERNEL_NAMES = {0: "mtgp_fast_kernel", 1: "mtgp_ring_kernel", 2: "mtgp_wide_kernel"}
+KERNEL_NAMES = {0: "mtgp_fast_kernel", 1: "mtgp_ring_kernel"}
 FORMATS = {"u32": 0, "f12": 1, "f01": 2}
 
 

@@ -232,11 +232,7 @@ typedef struct {
     uint32_t words_per_lane;  /* sub-steps per parallel step (2, 4 or 8); the
                                  window is 32 * words_per_lane <= N - pos      */
     uint32_t kernel;          /* 0 = register-resident path when available,
-                                 1 = shared-memory ring path (any parameters),
-                                 2 = register-resident, four consecutive columns
-                                 per lane and 128-bit output stores (needs
-                                 N - pos >= 256; warps_per_cta 4 or 8;
-                                 words_per_lane ignored; else as 0)           */
+                                 1 = shared-memory ring path (any parameters)  */
     uint32_t coop_percent;    /* streams of a launch longer than coop_percent/100
                                  times the numbers per warp slot are advanced
                                  by a whole CTA (longest first); 0 = never     */

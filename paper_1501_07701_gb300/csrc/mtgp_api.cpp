@@ -929,8 +929,8 @@ mtgp_status mtgp::validate_config(const mtgp_launch_config* c, LaunchCfg* out)
         return fail(MTGP_EINVAL, "warps_per_cta %u not in 1..8", c->warps_per_cta);
     if (c->words_per_lane != 2 && c->words_per_lane != 4 && c->words_per_lane != 8)
         return fail(MTGP_EINVAL, "words_per_lane %u not 2, 4 or 8", c->words_per_lane);
-    if (c->kernel > 2)
-        return fail(MTGP_EINVAL, "kernel %u not 0, 1 or 2", c->kernel);
+    if (c->kernel > 1)
+        return fail(MTGP_EINVAL, "kernel %u not 0 or 1", c->kernel);
     if (c->ctas_per_sm > 64)
         return fail(MTGP_EINVAL, "ctas_per_sm %u", c->ctas_per_sm);
     if (c->coop_percent > 100000)
@@ -987,24 +987,6 @@ std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
         if (k >= 8)
             add(8, k, 1, 100);
     }
-    // four consecutive columns per lane (128-word steps): 4 .. 16 warps per SM
-    auto add_wide = [&](int w, int cap) {
-        if (!wide_supported(P, w))
-            return;
-        LaunchCfg x;
-        x.warps_per_cta = w;
-        x.ctas_per_sm = cap;
-        x.k = 4;
-        x.kernel = 2;
-        x.coop_percent = 0;
-        v.push_back(x);
-    };
-    add_wide(8, 1);
-    add_wide(8, 2);
-    add_wide(4, 1);
-    add_wide(4, 2);
-    add_wide(4, 3);
-    add_wide(4, 4);
     if (v.empty()) {   // no register-resident instantiation: tune the ring kernel
         for (int w : {2, 4, 8}) {
             LaunchCfg x;

@@ -56,11 +56,10 @@ struct Segment {
 };
 
 struct LaunchCfg {
-    int warps_per_cta;   // G: 2, 4 or 8 for the register-resident kernels (1..8 ring)
+    int warps_per_cta;   // G: 2, 4 or 8 for the register-resident kernel (1..8 ring)
     int ctas_per_sm;     // 0 = occupancy maximum
     int k;               // sub-steps per parallel step (words per lane), 2, 4 or 8
-    int kernel;          // 0 register-resident, 1 shared-memory ring, 2 register-resident
-                         // with four consecutive columns per lane (128-word steps)
+    int kernel;          // 0 register-resident, 1 shared-memory ring
     int coop_percent;    // streams longer than coop_percent/100 x (numbers per warp
                          // slot) are advanced by a whole CTA; 0 = never
 };
@@ -75,8 +74,6 @@ __host__ __device__ inline uint32_t fast_smem_words(uint32_t n, uint32_t mirror)
     return (n + mirror + 3u) & ~3u;
 }
 __host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return 32u + ((n + 3u) & ~3u); }
-//   wide: the shared row in four interleaved sub-rows of ceil(N/4) words.
-__host__ __device__ inline uint32_t wide_smem_words(uint32_t n) { return ((n + 3u) >> 2) << 2; }
 
 // True if the register-resident kernel has an instantiation for this N, k
 // and g warps per CTA, the window 32*k fits (32*k <= N - pos), and the
@@ -137,14 +134,7 @@ cudaError_t launch_fast(int M, int K, int G, const GenArgs& a, dim3 grid, dim3 b
                         cudaStream_t s);
 const void* fast_kernel_ptr(int M, int K, int G);
 
-// Wide-column kernel (mtgp_wide.cuh): NS = ceil(N / 128) steps per row, G
-// warps per CTA.  Supported when N - pos >= 256, the shifts are in 1..31 and
-// NS has an instantiation.
-int wide_ns(const KParams& P);
-bool wide_supported(const KParams& P, int g = 8);
-const void* wide_kernel_ptr(int NS, int G);
-
-// Launches a generation kernel (fast or wide signature) by its pointer.
+// Launches a generation kernel with the register-resident kernel's signature.
 cudaError_t launch_gen_fn(const void* fn, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
                           cudaStream_t s);
 

@@ -208,15 +208,6 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
     int k = cfg.k;
     int kernel = cfg.kernel;
     int warps = std::max(1, std::min(8, cfg.warps_per_cta));
-    if (kernel == 2) {
-        // four consecutive columns per lane: G in {4, 8}; else the
-        // register-resident kernel
-        warps = warps <= 4 ? 4 : 8;
-        if (wide_supported(P, warps))
-            k = 4;
-        else
-            kernel = 0;
-    }
     if (kernel == 0) {
         // register-resident kernel: G in {2, 4, 8}
         warps = warps <= 2 ? 2 : (warps <= 4 ? 4 : 8);
@@ -239,9 +230,6 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
     if (kernel == 0) {
         g->smem = (size_t)warps * fast_smem_words(P.n, P.mirror) * 4u;
         fn = fast_kernel_ptr(fast_m(P), k, warps);
-    } else if (kernel == 2) {
-        g->smem = (size_t)warps * wide_smem_words(P.n) * 4u;
-        fn = wide_kernel_ptr(wide_ns(P), warps);
     } else {
         g->smem = (size_t)warps * ring_smem_words(P.n) * 4u;
         fn = (const void*)mtgp_ring_kernel;
@@ -280,12 +268,6 @@ cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
     if (g.kernel == 0)
         return launch_fast((int)((a.P.n + 31u) / 32u), g.k, g.threads / 32, a, dim3(g.grid),
                            dim3(g.threads), g.smem, s);
-    if (g.kernel == 2) {
-        const void* fn = wide_kernel_ptr(wide_ns(a.P), g.threads / 32);
-        if (!fn)
-            return cudaErrorInvalidValue;
-        return launch_gen_fn(fn, a, dim3(g.grid), dim3(g.threads), g.smem, s);
-    }
     mtgp_ring_kernel<<<g.grid, g.threads, g.smem, s>>>(a.P, a.states, a.n_streams, a.items, a.segs,
                                                        a.n_items, a.counter, a.out, a.err, a.sets,
                                                        a.set_of);
@@ -320,17 +302,6 @@ cudaError_t launch_fast(int M, int K, int G, const GenArgs& a, dim3 grid, dim3 b
     if (!fn)
         return cudaErrorInvalidValue;
     return launch_gen_fn(fn, a, grid, block, smem, s);
-}
-
-int wide_ns(const KParams& P) { return (int)((P.n + 127u) / 128u); }
-
-bool wide_supported(const KParams& P, int g)
-{
-    if (P.n < 257u || P.n - P.pos < 256u || P.pos < 1u)
-        return false;
-    if (P.sh1 < 1 || P.sh1 > 31 || P.sh2 < 1 || P.sh2 > 31)
-        return false;
-    return wide_kernel_ptr(wide_ns(P), g) != nullptr;
 }
 
 cudaError_t launch_gen_fn(const void* fn, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
