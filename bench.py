@@ -127,7 +127,7 @@ def rank_workload(args, rank: int, world: int):
     (stream seeds shifted by rank), so per-GPU work is fixed as ranks are
     added; strong: the contiguous range of one instance's streams that
     dist.strong_range gives this rank, so the job's work is fixed."""
-    if getattr(args, "split", "weak") == "strong" and world > 1:
+    if getattr(args, "rank_split", "weak") == "strong" and world > 1:
         w, desc = workload(args.workload, 0, args.streams, args.count, args.param_sets,
                            mexp=args.mexp)
         a, b = mdist.strong_range(w["seeds"].size, rank, world)
@@ -319,6 +319,9 @@ def run_ours(args, rank, world, local_rank):
                                     coop_percent=cv[2], ctas_per_sm=cv[3], kernel=cv[4])
     fmt = FORMATS[args.format]
     plan = mtgp.mtgp_plan_create(st, ids, counts, fmt, out)
+    max_piece = split_piece(args.split, total, torch.cuda.get_device_properties(dev).multi_processor_count)
+    if max_piece:
+        mtgp.mtgp_plan_set_split(plan, max_piece)
     tuned = None
     if not args.no_autotune and not args.config:
         tuned = mtgp.mtgp_plan_autotune(plan)
@@ -415,15 +418,17 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
-            "higher_is_better": True, "scaling": "strong" if args.split == "strong" else "weak",
+            "higher_is_better": True, "scaling": "strong" if args.rank_split == "strong" else "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": desc, "numbers_per_step_per_gpu": total, "format": args.format,
                        "parallelism": ("1 GPU" if world == 1 else
-                                       "one contiguous stream range per GPU" if args.split == "strong"
+                                       "one contiguous stream range per GPU" if args.rank_split == "strong"
                                        else "independent streams per GPU"),
                        "l2": "20 GB written per step (> 129 MB L2) plus a 256 MiB rewrite "
                              "between timed steps",
                        "launch": info["config"], "grid_ctas": info["grid_ctas"],
+                       "split": {"max_piece": info["max_piece"], "streams": info["n_split_streams"],
+                                 "jumps_per_launch": info["n_jumps"], "items": info["n_items"]},
                        "coop_streams": info["n_coop"], "regs_per_thread": info["regs_per_thread"],
                        "resident_ctas_per_sm": info["resident_ctas_per_sm"],
                        "autotuned": tuned is not None},
@@ -448,6 +453,17 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def split_piece(spec: str, total: int, sms: int) -> int:
+    """Piece length for --split: 0 (off), an explicit count, or 'auto' --
+    the numbers per warp slot at 16 warps per SM, so that no piece outlasts
+    an even share of the launch at that residency."""
+    if spec in ("", "0"):
+        return 0
+    if spec == "auto":
+        return max(64, -(-total // (sms * 16)))
+    return max(64, int(spec))
 
 
 def hbm_peak():
@@ -906,7 +922,11 @@ def main():
                     help="skip the equal/long workloads and the one-launch-per-stream comparison")
     ap.add_argument("--no-serving-parity", action="store_true",
                     help="skip the oracle replay of the serving trace's prefix")
-    ap.add_argument("--split", default="weak", choices=["weak", "strong"],
+    ap.add_argument("--split", default="0",
+                    help="cut streams longer than this many numbers into pieces started by exact "
+                         "jumps (mtgp_plan_set_split); 'auto' = the numbers per warp slot at 16 warps "
+                         "per SM; 0 = off")
+    ap.add_argument("--ranks", dest="rank_split", default="weak", choices=["weak", "strong"],
                     help="N > 1: weak = one workload instance per GPU; strong = one instance cut "
                          "into contiguous stream ranges")
     ap.add_argument("--mexp", type=int, default=0,

@@ -268,14 +268,34 @@ mtgp_status mtgp_plan_launch(mtgp_plan_t plan, void* cuda_stream);
 
 typedef struct {
     uint64_t total_numbers;   /* sum of counts                                 */
-    uint32_t n_items;         /* distinct streams in the plan                  */
+    uint32_t n_items;         /* items of the launched table: the plan's
+                                 streams, or pieces of split streams           */
     uint32_t kernel_launches; /* kernels per plan launch                       */
     mtgp_launch_config config;
     uint32_t grid_ctas;
     uint32_t n_coop;          /* streams advanced by whole CTAs                 */
     uint32_t regs_per_thread; /* of the generation kernel                       */
     uint32_t resident_ctas_per_sm;
+    uint64_t max_piece;       /* piece length of split streams (0 = no split)   */
+    uint32_t n_split_streams; /* streams cut into pieces                        */
+    uint32_t n_jumps;         /* jumps per launch (pieces after a first one)    */
 } mtgp_plan_info;
+
+/* Sec. 1 and Sec. 2 (one generator's stream shared out as sub-streams;
+ * streams persisting in global memory between launches): cuts every stream
+ * of the plan whose count exceeds max_piece into pieces of max_piece numbers
+ * (the last one shorter; at most 64 pieces per stream, longer streams get 64
+ * equal pieces), so that one long stream is advanced by several warps at
+ * once.  Each launch then copies every split stream's state into a scratch
+ * row per piece, advances the row of piece j by its offset j * max_piece
+ * with an exact jump (mtgp_jump's method; its polynomials are computed here,
+ * on the host, once per plan), and runs the generation kernel over the
+ * pieces, longest first; the stream's last piece leaves the stream's new
+ * state.  Outputs and states are exactly those of the unsplit plan.
+ * max_piece = 0 removes the split; 1 .. 63 is MTGP_EINVAL.  Re-records the
+ * plan's graph; synchronous.  The device scratch is one state row per
+ * piece, held by the plan. */
+mtgp_status mtgp_plan_set_split(mtgp_plan_t plan, uint64_t max_piece);
 
 /* Times the tuning candidates on this plan's own work table, on a scratch
  * copy of all states (the handle's states are not advanced; the plan's `out`

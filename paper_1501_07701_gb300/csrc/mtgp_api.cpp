@@ -334,7 +334,7 @@ mtgp_status mtgp::build_work(uint32_t n_streams, const uint32_t* ids, const uint
         WorkItem it;
         it.stream = sid;
         it.seg_begin = (uint32_t)w.segs.size();
-        it.pad = 0;
+        it.piece = 0;
         uint64_t g = 0;
         while (i < order.size() && ids[order[i]] == sid) {
             const uint32_t j = order[i];
@@ -394,6 +394,86 @@ void mtgp::fill_table(const Work& w, void* host)
         std::memcpy((char*)host + io, w.items.data(), w.items.size() * sizeof(WorkItem));
     if (!w.segs.empty())
         std::memcpy((char*)host + so, w.segs.data(), w.segs.size() * sizeof(Segment));
+}
+
+mtgp_status mtgp::split_work(const Work& w, uint64_t max_piece, uint32_t max_pieces,
+                             const std::vector<uint32_t>& set_of_stream, SplitWork* out)
+{
+    SplitWork& o = *out;
+    o = SplitWork();
+    o.max_piece = max_piece;
+    if (max_piece == 0) {
+        o.work = w;
+        return MTGP_OK;
+    }
+    struct Piece {
+        WorkItem it;
+        uint64_t total;
+        std::vector<Segment> segs;
+    };
+    std::vector<Piece> pieces;
+    for (size_t i = 0; i < w.items.size(); ++i) {
+        const WorkItem& it = w.items[i];
+        const uint64_t T = w.item_total[i];
+        const Segment* sg = w.segs.data() + it.seg_begin;
+        if (T <= max_piece) {
+            pieces.push_back(Piece{it, T, std::vector<Segment>(sg, sg + it.nseg)});
+            continue;
+        }
+        uint64_t L = max_piece;
+        uint64_t k = (T + L - 1) / L;
+        if (k > max_pieces) {
+            L = (T + max_pieces - 1) / max_pieces;
+            k = (T + L - 1) / L;
+        }
+        ++o.n_split;
+        const uint32_t set = set_of_stream.empty() ? 0u : set_of_stream[it.stream];
+        for (uint64_t j = 0; j < k; ++j) {
+            const uint64_t lo = j * L, hi = std::min(T, lo + L);
+            if (o.n_scratch >= kPieceRow - 1u)
+                return fail(MTGP_EINVAL, "too many pieces");
+            const uint32_t row = o.n_scratch++;
+            o.copies.push_back(make_uint2(it.stream, row));
+            if (j > 0) {
+                o.jump_rows.push_back(row);
+                o.jump_sets.push_back(set);
+                o.jump_lens.push_back(lo);
+            }
+            Piece p;
+            p.it = it;
+            p.it.piece = (row + 1u) | (j + 1 == k ? kPieceLast : 0u);
+            p.total = hi - lo;
+            for (uint32_t q = 0; q < it.nseg; ++q) {
+                const uint64_t a = std::max(sg[q].g_start, lo);
+                const uint64_t b = std::min(sg[q].g_start + sg[q].count, hi);
+                if (a >= b)
+                    continue;
+                Segment t = sg[q];
+                t.g_start = a - lo;
+                t.count = b - a;
+                t.out_off = sg[q].out_off + (a - sg[q].g_start);
+                p.segs.push_back(t);
+            }
+            pieces.push_back(std::move(p));
+        }
+    }
+    std::vector<size_t> order(pieces.size());
+    for (size_t i = 0; i < order.size(); ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return pieces[a].total > pieces[b].total; });
+    Work& ow = o.work;
+    for (size_t i : order) {
+        Piece& p = pieces[i];
+        p.it.seg_begin = (uint32_t)ow.segs.size();
+        p.it.nseg = (uint32_t)p.segs.size();
+        ow.segs.insert(ow.segs.end(), p.segs.begin(), p.segs.end());
+        ow.items.push_back(p.it);
+        ow.item_total.push_back(p.total);
+        ow.total += p.total;
+        ow.max_item = std::max(ow.max_item, p.total);
+    }
+    return MTGP_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -678,19 +758,19 @@ mtgp_status mtgp::geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t 
 
 // Uploads a work table through the handle's slot ring and launches.
 mtgp_status mtgp::launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
-                              cudaStream_t s)
+                              cudaStream_t s, uint32_t* scratch)
 {
     if (w.items.empty())
         return MTGP_OK;
     TableSlot& sl = st->slots[st->next_slot];
     st->next_slot = (st->next_slot + 1) % (int)st->slots.size();
-    return launch_work_slot(st, sl, w, cfg, out, s);
+    return launch_work_slot(st, sl, w, cfg, out, s, scratch);
 }
 
 // Uploads a work table through `sl` (waiting for the slot's previous
 // consumer) and launches on `s`; records the slot's event after the kernel.
 mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w,
-                                   const LaunchCfg& cfg, void* out, cudaStream_t s)
+                                   const LaunchCfg& cfg, void* out, cudaStream_t s, uint32_t* scratch)
 {
     if (w.items.empty())
         return MTGP_OK;
@@ -734,6 +814,7 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
     a.trace = nullptr;
     a.sets = st->d_sets;
     a.set_of = st->d_set_of;
+    a.scratch = scratch;
     CUDA_TRY(launch_generate(a, g, s), "generation kernel launch");
     CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
     sl.ev_recorded = true;
@@ -1003,7 +1084,7 @@ std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
 
 // Times one configuration on scratch states: best of `reps` launches.
 mtgp_status mtgp::time_config(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, uint32_t* states,
-                              void* out, int reps, float* best_ms)
+                              void* out, int reps, float* best_ms, uint32_t* scratch)
 {
     cudaStream_t s = st->tune_stream;
     cudaEvent_t a = st->tune_ev[0], b = st->tune_ev[1];
@@ -1013,7 +1094,7 @@ mtgp_status mtgp::time_config(mtgp_streams* st, const Work& w, const LaunchCfg& 
     mtgp_status r = MTGP_OK;
     for (int i = 0; i < reps + 1 && r == MTGP_OK; ++i) {
         cudaEventRecord(a, s);
-        r = launch_work(st, w, cfg, out, s);
+        r = launch_work(st, w, cfg, out, s, scratch);
         cudaEventRecord(b, s);
         if (r != MTGP_OK)
             break;
@@ -1144,8 +1225,18 @@ static mtgp_status record_graph(mtgp_plan* p)
     if (p->n_items == 0)
         return MTGP_OK;
     cudaStream_t cap = p->cap_stream;
+    const uint32_t n_copies = (uint32_t)p->split.copies.size();
+    const uint32_t n_jumps = (uint32_t)p->jumps.items.size();
     CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    cudaError_t e1 = cudaMemsetAsync(p->d_table, 0, 2 * sizeof(uint32_t), cap);
+    // split streams: every piece gets its stream's state, then the pieces
+    // after the first are jumped to their offsets
+    cudaError_t e1 = launch_copy_rows(p->st->d_states, p->d_scratch, p->d_copies, n_copies,
+                                      p->st->P.k.n, p->st->P.k.np, cap);
+    if (e1 == cudaSuccess)
+        e1 = launch_jump_batch(p->st, p->d_scratch, p->d_jitems, n_jumps, p->d_jpolys, p->jumps.words,
+                               p->jumps.smem, cap);
+    if (e1 == cudaSuccess)
+        e1 = cudaMemsetAsync(p->d_table, 0, 2 * sizeof(uint32_t), cap);
     GenArgs a;
     a.P = p->st->P.k;
     a.states = p->st->d_states;
@@ -1153,7 +1244,7 @@ static mtgp_status record_graph(mtgp_plan* p)
     a.items = (const WorkItem*)((char*)p->d_table + p->items_off);
     a.segs = (const Segment*)((char*)p->d_table + p->segs_off);
     a.n_items = p->n_items;
-    a.n_coop = p->st->d_sets ? 0u : coop_count(p->work, p->geo, p->cfg.coop_percent);
+    a.n_coop = p->st->d_sets ? 0u : coop_count(p->split.work, p->geo, p->cfg.coop_percent);
     p->n_coop = a.n_coop;
     a.counter = (uint32_t*)p->d_table;
     a.out = (uint32_t*)p->out;
@@ -1161,6 +1252,7 @@ static mtgp_status record_graph(mtgp_plan* p)
     a.trace = p->d_trace;
     a.sets = p->st->d_sets;
     a.set_of = p->st->d_set_of;
+    a.scratch = p->d_scratch;
     cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, p->geo, cap) : e1;
     cudaGraph_t graph = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(cap, &graph);
@@ -1173,8 +1265,86 @@ static mtgp_status record_graph(mtgp_plan* p)
         return fail_cuda(e3, "cudaStreamEndCapture");
     p->graph = graph;
     CUDA_TRY(cudaGraphInstantiate(&p->exec, graph, 0), "cudaGraphInstantiate");
-    p->kernel_launches = 1;
+    p->kernel_launches = 1 + (n_copies ? 1u : 0u) + (n_jumps ? 1u : 0u);
     return MTGP_OK;
+}
+
+// Frees the device side of a plan's split (scratch rows, copy pairs, jump
+// items and polynomials).
+static void free_split(mtgp_plan* p)
+{
+    if (p->d_scratch)
+        cudaFree(p->d_scratch);
+    if (p->d_copies)
+        cudaFree(p->d_copies);
+    if (p->d_jitems)
+        cudaFree(p->d_jitems);
+    if (p->d_jpolys)
+        cudaFree(p->d_jpolys);
+    p->d_scratch = nullptr;
+    p->d_copies = nullptr;
+    p->d_jitems = nullptr;
+    p->d_jpolys = nullptr;
+    p->jumps = JumpBatch();
+}
+
+// (Re)builds what a plan launches from its requests and max_piece: the work
+// table (pieces when split), and for split plans the scratch rows, copy
+// pairs and jumps.  Device memory of the previous build is released.
+static mtgp_status build_launch(mtgp_plan* p, uint64_t max_piece)
+{
+    mtgp_streams* st = p->st;
+    std::vector<uint32_t> set_of_stream;
+    if (st->d_sets && max_piece) {
+        set_of_stream.resize(st->n_streams);
+        CUDA_TRY(cudaMemcpy(set_of_stream.data(), st->d_set_of, st->n_streams * 4, cudaMemcpyDeviceToHost),
+                 "cudaMemcpy(set index)");
+    }
+    SplitWork sw;
+    mtgp_status r = split_work(p->work, max_piece, 64, set_of_stream, &sw);
+    if (r != MTGP_OK)
+        return r;
+    JumpBatch jb;
+    r = build_jump_batch(st, sw.jump_rows, sw.jump_sets, sw.jump_lens, &jb);
+    if (r != MTGP_OK)
+        return r;
+    CUDA_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    free_split(p);
+    if (p->d_table) {
+        cudaFree(p->d_table);
+        p->d_table = nullptr;
+    }
+    const size_t bytes = table_bytes(sw.work, &p->items_off, &p->segs_off);
+    std::vector<char> host(bytes);
+    fill_table(sw.work, host.data());
+    CUDA_TRY(cudaMalloc(&p->d_table, bytes), "cudaMalloc(plan table)");
+    CUDA_TRY(cudaMemcpy(p->d_table, host.data(), bytes, cudaMemcpyHostToDevice), "cudaMemcpy(plan table)");
+    if (sw.n_scratch) {
+        const size_t rows = (size_t)sw.n_scratch * st->P.k.np * 4;
+        CUDA_TRY(cudaMalloc(&p->d_scratch, rows), "cudaMalloc(piece states)");
+        CUDA_TRY(cudaMalloc(&p->d_copies, sw.copies.size() * sizeof(uint2)), "cudaMalloc(copy pairs)");
+        CUDA_TRY(cudaMemcpy(p->d_copies, sw.copies.data(), sw.copies.size() * sizeof(uint2),
+                            cudaMemcpyHostToDevice), "cudaMemcpy(copy pairs)");
+    }
+    if (!jb.items.empty()) {
+        CUDA_TRY(cudaMalloc(&p->d_jitems, jb.items.size() * sizeof(JumpItem)), "cudaMalloc(jump items)");
+        CUDA_TRY(cudaMemcpy(p->d_jitems, jb.items.data(), jb.items.size() * sizeof(JumpItem),
+                            cudaMemcpyHostToDevice), "cudaMemcpy(jump items)");
+        CUDA_TRY(cudaMalloc(&p->d_jpolys, jb.poly_words.size() * 4), "cudaMalloc(jump polynomials)");
+        CUDA_TRY(cudaMemcpy(p->d_jpolys, jb.poly_words.data(), jb.poly_words.size() * 4,
+                            cudaMemcpyHostToDevice), "cudaMemcpy(jump polynomials)");
+    }
+    p->split = std::move(sw);
+    p->jumps = std::move(jb);
+    p->n_items = (uint32_t)p->split.work.items.size();
+    p->max_item = p->split.work.max_item;
+    if (p->d_trace) {   // one record per launched item
+        cudaFree(p->d_trace);
+        p->d_trace = nullptr;
+        CUDA_TRY(cudaMalloc(&p->d_trace, (size_t)p->n_items * 4 * sizeof(uint64_t)), "cudaMalloc(trace)");
+        CUDA_TRY(cudaMemset(p->d_trace, 0, (size_t)p->n_items * 4 * sizeof(uint64_t)), "cudaMemset");
+    }
+    return geometry_for(st, p->cfg, p->n_items, &p->geo);
 }
 
 static void destroy_plan(mtgp_plan* p)
@@ -1192,6 +1362,7 @@ static void destroy_plan(mtgp_plan* p)
         cudaFree(p->d_table);
     if (p->d_trace)
         cudaFree(p->d_trace);
+    free_split(p);
     delete p;
 }
 
@@ -1225,14 +1396,7 @@ extern "C" mtgp_status mtgp_plan_create(mtgp_streams_t st, const uint32_t* ids, 
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(fail_cuda(e, "cudaStreamCreate"));
-    const size_t bytes = table_bytes(w, &p->items_off, &p->segs_off);
-    std::vector<char> host(bytes);
-    fill_table(w, host.data());
-    if ((e = cudaMalloc(&p->d_table, bytes)) != cudaSuccess)
-        return bail(fail_cuda(e, "cudaMalloc(plan table)"));
-    if ((e = cudaMemcpy(p->d_table, host.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(fail_cuda(e, "cudaMemcpy(plan table)"));
-    s = geometry_for(st, p->cfg, p->n_items, &p->geo);
+    s = build_launch(p, 0);
     if (s != MTGP_OK)
         return bail(s);
     s = record_graph(p);
@@ -1286,7 +1450,7 @@ extern "C" mtgp_status mtgp_plan_autotune(mtgp_plan_t p, mtgp_launch_config* bes
             if (geometry_for(st, c, 1, &probe) != MTGP_OK)
                 continue;   // not launchable on this device (registers or shared memory)
             float ms = 0;
-            r = time_config(st, p->work, c, scratch, p->out, 2, &ms);
+            r = time_config(st, p->split.work, c, scratch, p->out, 2, &ms, p->d_scratch);
             if (r != MTGP_OK) {
                 r = fail_candidate(r, c);
                 break;
@@ -1351,12 +1515,33 @@ extern "C" mtgp_status mtgp_plan_read_trace(mtgp_plan_t p, uint64_t* host)
     GUARD_END
 }
 
+extern "C" mtgp_status mtgp_plan_set_split(mtgp_plan_t p, uint64_t max_piece)
+{
+    GUARD_BEGIN
+    if (!p)
+        return fail(MTGP_EINVAL, "null plan");
+    if (max_piece != 0 && max_piece < 64)
+        return fail(MTGP_EINVAL, "max_piece %llu below 64", (unsigned long long)max_piece);
+    DeviceGuard g(p->st->device);
+    mtgp_status r = build_launch(p, max_piece);
+    if (r != MTGP_OK)
+        return r;
+    r = record_graph(p);
+    if (r != MTGP_OK)
+        return r;
+    return ok();
+    GUARD_END
+}
+
 extern "C" mtgp_status mtgp_plan_get_info(mtgp_plan_t p, mtgp_plan_info* info)
 {
     if (!p || !info)
         return fail(MTGP_EINVAL, "null argument");
     info->total_numbers = p->total;
     info->n_items = p->n_items;
+    info->max_piece = p->split.max_piece;
+    info->n_split_streams = p->split.n_split;
+    info->n_jumps = (uint32_t)p->jumps.items.size();
     info->kernel_launches = p->kernel_launches;
     LaunchCfg eff = p->cfg;
     eff.kernel = p->geo.kernel;

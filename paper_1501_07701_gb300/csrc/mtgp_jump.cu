@@ -381,13 +381,6 @@ const Poly* cached_mu(const Rec& p, uint32_t mexp)
 // and the N-word accumulator.  Every wait is a __syncthreads on uniform
 // control flow; no spin waits.
 // ---------------------------------------------------------------------------
-struct JumpItem {
-    uint32_t stream;
-    uint32_t poly;       // index of g among the launch's polynomials
-    uint32_t deg;        // deg g (g != 0)
-    uint32_t set;        // parameter-set index (per-stream sets) or 0
-};
-
 __global__ void __launch_bounds__(256) mtgp_jump_kernel(const KParams P, uint32_t* __restrict__ states,
                                                        const JumpItem* __restrict__ items,
                                                        const uint32_t* __restrict__ polys,
@@ -743,6 +736,134 @@ extern "C" mtgp_status mtgp_mt_params_period_check(const mtgp_mt_params* params,
     }
 }
 
+// The jump polynomials g = t^(J-1) mod mu of one parameter set for the
+// lengths J (sorted, distinct), cached.  Consecutive lengths reuse each
+// other: t^(J'-1) = t^(J-1) * t^(J'-J) mod mu, so a run of equally spaced
+// lengths costs one power and one product per length.
+static std::vector<const Poly*> jump_polys(const SetP& p, const Poly& mu, const std::vector<uint64_t>& J)
+{
+    std::vector<const Poly*> out(J.size(), nullptr);
+    const auto key = key_of(p);
+    std::map<uint64_t, Poly> step;   // t^d mod mu for the gaps d between lengths
+    const Poly* prev = nullptr;
+    uint64_t prev_j = 0;
+    for (size_t i = 0; i < J.size(); ++i) {
+        const auto jk = std::make_pair(key, J[i]);
+        {
+            std::lock_guard<std::mutex> g(g_cache_mutex);
+            auto it = g_jump_cache.find(jk);
+            if (it != g_jump_cache.end())
+                out[i] = &it->second;
+        }
+        if (!out[i]) {
+            Poly g;
+            if (prev) {
+                const uint64_t d = J[i] - prev_j;
+                auto st = step.find(d);
+                if (st == step.end())
+                    st = step.emplace(d, pow_t_mod(d, mu)).first;
+                g = mod(mul(*prev, st->second), mu);
+            } else {
+                g = pow_t_mod(J[i] - 1, mu);
+            }
+            if (degree(g) < 0)
+                g.assign(1, 0);
+            std::lock_guard<std::mutex> lk(g_cache_mutex);
+            out[i] = &g_jump_cache.emplace(jk, std::move(g)).first->second;
+        }
+        prev = out[i];
+        prev_j = J[i];
+    }
+    return out;
+}
+
+mtgp_status mtgp::build_jump_batch(mtgp_streams* st, const std::vector<uint32_t>& rows,
+                                   const std::vector<uint32_t>& sets, const std::vector<uint64_t>& jumps,
+                                   JumpBatch* out)
+{
+    out->items.clear();
+    out->poly_words.clear();
+    out->words = 0;
+    out->smem = 0;
+    std::vector<KSet> host_sets;
+    if (st->d_sets) {
+        host_sets.resize(st->n_sets);
+        const cudaError_t e = cudaMemcpy(host_sets.data(), st->d_sets, st->n_sets * sizeof(KSet),
+                                         cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return fail_cuda(e, "cudaMemcpy(parameter sets)");
+    }
+    // distinct lengths per parameter set
+    std::map<uint32_t, std::vector<uint64_t>> lengths;
+    for (size_t i = 0; i < rows.size(); ++i)
+        if (jumps[i])
+            lengths[sets[i]].push_back(jumps[i]);
+    std::map<std::pair<uint32_t, uint64_t>, uint32_t> poly_index;
+    std::vector<const Poly*> polys;
+    for (auto& kv : lengths) {
+        std::sort(kv.second.begin(), kv.second.end());
+        kv.second.erase(std::unique(kv.second.begin(), kv.second.end()), kv.second.end());
+        const SetP p = set_of(st->P.k, st->d_sets ? &host_sets[kv.first] : nullptr);
+        const Poly* mu = cached_mu(p, st->P.d.mexp);
+        if (!mu)
+            return fail(MTGP_EINVAL, "no annihilating polynomial found for parameter set %u", kv.first);
+        const std::vector<const Poly*> g = jump_polys(p, *mu, kv.second);
+        for (size_t i = 0; i < g.size(); ++i) {
+            poly_index.emplace(std::make_pair(kv.first, kv.second[i]), (uint32_t)polys.size());
+            polys.push_back(g[i]);
+        }
+    }
+    uint32_t max_deg = 0;
+    for (size_t i = 0; i < rows.size(); ++i) {
+        if (!jumps[i])
+            continue;
+        const uint32_t pi = poly_index.at(std::make_pair(sets[i], jumps[i]));
+        JumpItem ji;
+        ji.stream = rows[i];
+        ji.poly = pi;
+        ji.deg = (uint32_t)std::max(degree(*polys[pi]), 0);
+        ji.set = sets[i];
+        out->items.push_back(ji);
+        max_deg = std::max(max_deg, ji.deg);
+    }
+    if (out->items.empty())
+        return MTGP_OK;
+    const uint32_t N = st->P.k.n;
+    out->words = (max_deg + 1 + 31) / 32;
+    out->poly_words.assign(polys.size() * (size_t)out->words, 0u);
+    for (size_t i = 0; i < polys.size(); ++i)
+        for (int k = 0; k <= degree(*polys[i]); ++k)
+            if (bit(*polys[i], (size_t)k))
+                out->poly_words[i * out->words + (size_t)k / 32] |= 1u << (k % 32);
+    // a zero g (possible only if t^(J-1) = 0 mod mu, which needs t | mu):
+    // the kernel then accumulates nothing and applies one step to 0
+    out->smem = ((size_t)max_deg + 1 + N - 1 + N) * 4;
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "device attributes");
+    if (out->smem + 64 > (size_t)max_smem)
+        return fail(MTGP_EINVAL, "state size too large for the jump kernel (%zu bytes of shared memory)",
+                    out->smem);
+    e = cudaFuncSetAttribute((const void*)mtgp_jump_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)out->smem);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "cudaFuncSetAttribute(jump kernel)");
+    return MTGP_OK;
+}
+
+cudaError_t mtgp::launch_jump_batch(const mtgp_streams* st, uint32_t* rows_base, const JumpItem* d_items,
+                                    uint32_t n, const uint32_t* d_polys, uint32_t words, size_t smem,
+                                    cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    mtgp_jump_kernel<<<n, 256, smem, s>>>(st->P.k, rows_base, d_items, d_polys, words, st->d_sets);
+    return cudaGetLastError();
+}
+
 extern "C" mtgp_status mtgp_jump(mtgp_streams_t st, const uint32_t* ids, const uint64_t* jumps, uint32_t n,
                                  void* cuda_stream)
 {
@@ -762,92 +883,37 @@ extern "C" mtgp_status mtgp_jump(mtgp_streams_t st, const uint32_t* ids, const u
         }
         // set index of each stream (per-stream parameter sets)
         std::vector<uint32_t> set_of_stream;
-        std::vector<KSet> host_sets;
         if (st->d_sets) {
             set_of_stream.resize(st->n_streams);
-            host_sets.resize(st->n_sets);
             J_TRY(cudaMemcpy(set_of_stream.data(), st->d_set_of, st->n_streams * 4, cudaMemcpyDeviceToHost),
                   "cudaMemcpy(set index)");
-            J_TRY(cudaMemcpy(host_sets.data(), st->d_sets, st->n_sets * sizeof(KSet), cudaMemcpyDeviceToHost),
-                  "cudaMemcpy(parameter sets)");
         }
-        std::vector<JumpItem> items;
-        std::vector<const Poly*> polys;
-        std::map<std::pair<uint32_t, uint64_t>, uint32_t> poly_index;
-        uint32_t max_deg = 0;
+        std::vector<uint32_t> rows, sets;
+        std::vector<uint64_t> lens;
         for (const auto& kv : total) {
-            if (kv.second == 0)
-                continue;
-            const uint32_t set = st->d_sets ? set_of_stream[kv.first] : 0u;
-            const auto pk = std::make_pair(set, kv.second);
-            auto pit = poly_index.find(pk);
-            if (pit == poly_index.end()) {
-                const SetP p = set_of(st->P.k, st->d_sets ? &host_sets[set] : nullptr);
-                const Poly* mu = cached_mu(p, st->P.d.mexp);
-                if (!mu)
-                    return fail(MTGP_EINVAL, "no annihilating polynomial found for parameter set %u", set);
-                const auto jk = std::make_pair(key_of(p), kv.second);
-                const Poly* gp = nullptr;
-                {
-                    std::lock_guard<std::mutex> g(g_cache_mutex);
-                    auto it = g_jump_cache.find(jk);
-                    if (it != g_jump_cache.end())
-                        gp = &it->second;
-                }
-                if (!gp) {
-                    Poly gpoly = pow_t_mod(kv.second - 1, *mu);
-                    if (degree(gpoly) < 0)
-                        gpoly.assign(1, 0);
-                    std::lock_guard<std::mutex> g(g_cache_mutex);
-                    gp = &g_jump_cache.emplace(jk, std::move(gpoly)).first->second;
-                }
-                pit = poly_index.emplace(pk, (uint32_t)polys.size()).first;
-                polys.push_back(gp);
-            }
-            const int d = std::max(degree(*polys[pit->second]), 0);
-            JumpItem ji;
-            ji.stream = kv.first;
-            ji.poly = pit->second;
-            ji.deg = (uint32_t)d;
-            ji.set = set;
-            items.push_back(ji);
-            max_deg = std::max(max_deg, (uint32_t)d);
+            rows.push_back(kv.first);
+            sets.push_back(st->d_sets ? set_of_stream[kv.first] : 0u);
+            lens.push_back(kv.second);
         }
-        if (items.empty())
+        JumpBatch b;
+        mtgp_status r = build_jump_batch(st, rows, sets, lens, &b);
+        if (r != MTGP_OK)
+            return r;
+        if (b.items.empty())
             return ok();
-        const uint32_t N = st->P.k.n;
-        const uint32_t poly_words = (max_deg + 1 + 31) / 32;
-        std::vector<uint32_t> pw(polys.size() * (size_t)poly_words, 0u);
-        for (size_t i = 0; i < polys.size(); ++i)
-            for (int k = 0; k <= degree(*polys[i]); ++k)
-                if (bit(*polys[i], (size_t)k))
-                    pw[i * poly_words + (size_t)k / 32] |= 1u << (k % 32);
-        // a zero g (possible only if t^(J-1) = 0 mod mu, which needs t | mu):
-        // the kernel then accumulates nothing and applies one step to 0
-        const size_t smem = ((size_t)max_deg + 1 + N - 1 + N) * 4;
-        int dev = 0, max_smem = 0;
-        J_TRY(cudaGetDevice(&dev), "cudaGetDevice");
-        J_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
-              "cudaDeviceGetAttribute");
-        if (smem + 64 > (size_t)max_smem)
-            return fail(MTGP_EINVAL, "state size too large for the jump kernel (%zu bytes of shared memory)", smem);
-        J_TRY(cudaFuncSetAttribute((const void*)mtgp_jump_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem), "cudaFuncSetAttribute");
         cudaStream_t cs = (cudaStream_t)cuda_stream;
         void *d_items = nullptr, *d_polys = nullptr;
-        J_TRY(cudaMallocAsync(&d_items, items.size() * sizeof(JumpItem), cs), "cudaMallocAsync");
-        cudaError_t e = cudaMallocAsync(&d_polys, pw.size() * 4, cs);
+        J_TRY(cudaMallocAsync(&d_items, b.items.size() * sizeof(JumpItem), cs), "cudaMallocAsync");
+        cudaError_t e = cudaMallocAsync(&d_polys, b.poly_words.size() * 4, cs);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(JumpItem), cudaMemcpyHostToDevice, cs);
+            e = cudaMemcpyAsync(d_items, b.items.data(), b.items.size() * sizeof(JumpItem),
+                                cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_polys, pw.data(), pw.size() * 4, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) {
-            mtgp_jump_kernel<<<(unsigned)items.size(), 256, smem, cs>>>(st->P.k, st->d_states,
-                                                                        (const JumpItem*)d_items,
-                                                                        (const uint32_t*)d_polys, poly_words,
-                                                                        st->d_sets);
-            e = cudaGetLastError();
-        }
+            e = cudaMemcpyAsync(d_polys, b.poly_words.data(), b.poly_words.size() * 4,
+                                cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = launch_jump_batch(st, st->d_states, (const JumpItem*)d_items, (uint32_t)b.items.size(),
+                                  (const uint32_t*)d_polys, b.words, b.smem, cs);
         // the host arrays above are locals: wait for the copies before returning
         const cudaError_t e2 = cudaStreamSynchronize(cs);
         if (d_polys)

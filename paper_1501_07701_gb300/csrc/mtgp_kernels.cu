@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
                                                         uint32_t n_items, uint32_t* __restrict__ counter,
                                                         uint32_t* __restrict__ out, int* __restrict__ err,
                                                         const KSet* __restrict__ sets,
-                                                        const uint32_t* __restrict__ set_of)
+                                                        const uint32_t* __restrict__ set_of,
+                                                        uint32_t* __restrict__ scratch)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
@@ -112,7 +113,8 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
             tmp[lane] = P.tmp[lane];
         }
         const uint32_t Wc = (N - pos) < 32u ? (N - pos) : 32u;
-        uint32_t* g = states + (size_t)w.stream * P.np;
+        uint32_t *g, *g_out;
+        item_rows(w, states, scratch, P.np, &g, &g_out);
         for (uint32_t j = lane; j < N; j += 32u)
             S[j] = g[j];
         __syncwarp();
@@ -166,10 +168,40 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
         for (uint32_t j = lane; j < N; j += 32u) {
             uint32_t c = phase + j;
             c = c >= N ? c - N : c;
-            g[j] = S[c];
+            g_out[j] = S[c];
         }
         __syncwarp();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Row copies (the start states of a split stream's pieces): one warp per
+// pair, grid-stride over pairs.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) mtgp_copy_rows_kernel(const uint32_t* __restrict__ src,
+                                                            uint32_t* __restrict__ dst,
+                                                            const uint2* __restrict__ pairs,
+                                                            uint32_t n, uint32_t N, uint32_t np)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const uint2 p = pairs[i];
+        const uint32_t* a = src + (size_t)p.x * np;
+        uint32_t* b = dst + (size_t)p.y * np;
+        for (uint32_t j = lane; j < N; j += 32u)
+            b[j] = a[j];
+    }
+}
+
+cudaError_t launch_copy_rows(const uint32_t* src, uint32_t* dst, const uint2* pairs, uint32_t n,
+                             uint32_t N, uint32_t np, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const uint32_t blocks = std::min<uint32_t>((n + 7u) / 8u, 1024u);
+    mtgp_copy_rows_kernel<<<blocks, 256, 0, s>>>(src, dst, pairs, n, N, np);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -270,7 +302,7 @@ cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
                            dim3(g.threads), g.smem, s);
     mtgp_ring_kernel<<<g.grid, g.threads, g.smem, s>>>(a.P, a.states, a.n_streams, a.items, a.segs,
                                                        a.n_items, a.counter, a.out, a.err, a.sets,
-                                                       a.set_of);
+                                                       a.set_of, a.scratch);
     return cudaGetLastError();
 }
 
@@ -320,8 +352,9 @@ cudaError_t launch_gen_fn(const void* fn, const GenArgs& a, dim3 grid, dim3 bloc
     uint64_t* trace = a.trace;
     const KSet* sets = a.sets;
     const uint32_t* set_of = a.set_of;
+    uint32_t* scratch = a.scratch;
     void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &n_coop, &counter, &out, &err,
-                    &trace, &sets, &set_of};
+                    &trace, &sets, &set_of, &scratch};
     return cudaLaunchKernel(fn, grid, block, args, smem, s);
 }
 

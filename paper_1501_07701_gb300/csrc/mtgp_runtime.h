@@ -92,6 +92,35 @@ struct mtgp_streams {
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
 };
 
+namespace mtgp {
+
+// Jumps of state rows prepared on the host: items and the bit table of their
+// polynomials (`words` 32-bit words each), and the jump kernel's dynamic
+// shared memory.
+struct JumpBatch {
+    std::vector<JumpItem> items;
+    std::vector<uint32_t> poly_words;
+    uint32_t words = 0;
+    size_t smem = 0;
+};
+
+// A launch whose longest streams are cut into pieces: `work` holds the
+// pieces as items (see WorkItem::piece); before the generation kernel,
+// `copies` (stream row -> scratch row) give every piece its stream's state
+// and `jumps` advance the scratch rows of pieces after the first by the
+// piece's offset in the stream.
+struct SplitWork {
+    Work work;
+    uint64_t max_piece = 0;        // 0 = not split
+    uint32_t n_scratch = 0;        // scratch state rows
+    uint32_t n_split = 0;          // streams cut into pieces
+    std::vector<uint2> copies;
+    std::vector<uint32_t> jump_rows, jump_sets;
+    std::vector<uint64_t> jump_lens;
+};
+
+}  // namespace mtgp
+
 struct mtgp_plan {
     mtgp_streams* st = nullptr;
     void* out = nullptr;
@@ -101,7 +130,14 @@ struct mtgp_plan {
     uint64_t max_item = 0;
     mtgp::LaunchCfg cfg{};
     mtgp::Geometry geo{};
-    mtgp::Work work;
+    mtgp::Work work;               // the requests, one item per stream
+    mtgp::SplitWork split;         // the launched work (pieces when split)
+    // split launches: scratch rows, copy pairs, jump items and polynomials
+    uint32_t* d_scratch = nullptr;
+    uint2* d_copies = nullptr;
+    mtgp::JumpItem* d_jitems = nullptr;
+    uint32_t* d_jpolys = nullptr;
+    mtgp::JumpBatch jumps;
     void* d_table = nullptr;
     uint64_t* d_trace = nullptr;   // optional per-item timeline
     size_t items_off = 0, segs_off = 0;
@@ -124,15 +160,32 @@ void fill_table(const Work& w, void* host);
 LaunchCfg default_config(const KParams& P);
 mtgp_status geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t n_items, Geometry* g);
 mtgp_status launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
-                        cudaStream_t s);
+                        cudaStream_t s, uint32_t* scratch = nullptr);
 mtgp_status launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w, const LaunchCfg& cfg,
-                             void* out, cudaStream_t s);
+                             void* out, cudaStream_t s, uint32_t* scratch = nullptr);
 void free_table_slot(TableSlot& s);
 mtgp_status validate_config(const mtgp_launch_config* c, LaunchCfg* out);
 // Number of leading (longest) items a launch hands to whole CTAs.
 uint32_t coop_count(const Work& w, const Geometry& g, int coop_percent);
 std::vector<LaunchCfg> tuning_candidates(const KParams& P);
 mtgp_status time_config(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, uint32_t* states,
-                        void* out, int reps, float* best_ms);
+                        void* out, int reps, float* best_ms, uint32_t* scratch = nullptr);
+
+// Cuts the items of `w` longer than max_piece numbers into pieces of
+// max_piece numbers (the last one shorter), at most max_pieces per stream
+// (longer streams get equal pieces of ceil(total / max_pieces)), and sorts
+// all items longest first.  set_of_stream: per-stream parameter set index
+// (empty for one shared set).
+mtgp_status split_work(const Work& w, uint64_t max_piece, uint32_t max_pieces,
+                       const std::vector<uint32_t>& set_of_stream, SplitWork* out);
+
+// Jump polynomials and items for advancing rows[i] (of the array the launch
+// is given) by jumps[i] numbers (0 = no jump); sets[i] = parameter set index.
+mtgp_status build_jump_batch(mtgp_streams* st, const std::vector<uint32_t>& rows,
+                             const std::vector<uint32_t>& sets, const std::vector<uint64_t>& jumps,
+                             JumpBatch* out);
+cudaError_t launch_jump_batch(const mtgp_streams* st, uint32_t* rows_base, const JumpItem* d_items,
+                              uint32_t n, const uint32_t* d_polys, uint32_t words, size_t smem,
+                              cudaStream_t s);
 
 }  // namespace mtgp

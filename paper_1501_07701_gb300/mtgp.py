@@ -51,7 +51,9 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("total_numbers", ctypes.c_uint64), ("n_items", ctypes.c_uint32),
                 ("kernel_launches", ctypes.c_uint32), ("config", LaunchConfig),
                 ("grid_ctas", ctypes.c_uint32), ("n_coop", ctypes.c_uint32),
-                ("regs_per_thread", ctypes.c_uint32), ("resident_ctas_per_sm", ctypes.c_uint32)]
+                ("regs_per_thread", ctypes.c_uint32), ("resident_ctas_per_sm", ctypes.c_uint32),
+                ("max_piece", ctypes.c_uint64), ("n_split_streams", ctypes.c_uint32),
+                ("n_jumps", ctypes.c_uint32)]
 
 
 class MtParams(ctypes.Structure):
@@ -117,6 +119,7 @@ _SIGS = {
     "mtgp_plan_create": [_VP, _U32P, _U64P, ctypes.c_uint32, ctypes.c_int, _VP,
                          ctypes.POINTER(_VP)],
     "mtgp_plan_launch": [_VP, _VP],
+    "mtgp_plan_set_split": [_VP, ctypes.c_uint64],
     "mtgp_plan_autotune": [_VP, ctypes.POINTER(LaunchConfig)],
     "mtgp_plan_get_info": [_VP, ctypes.POINTER(PlanInfo)],
     "mtgp_plan_set_trace": [_VP, ctypes.c_int],
@@ -433,6 +436,10 @@ def mtgp_plan_launch(plan: Plan, stream=None):
     _call("mtgp_plan_launch", plan.handle, _stream_handle(stream))
 
 
+def mtgp_plan_set_split(plan: Plan, max_piece: int):
+    _call("mtgp_plan_set_split", plan.handle, int(max_piece))
+
+
 def mtgp_plan_autotune(plan: Plan) -> dict:
     c = LaunchConfig()
     _call("mtgp_plan_autotune", plan.handle, ctypes.byref(c))
@@ -457,7 +464,8 @@ def mtgp_plan_get_info(plan: Plan) -> dict:
     return {"total_numbers": i.total_numbers, "n_items": i.n_items,
             "kernel_launches": i.kernel_launches, "config": i.config.as_dict(),
             "grid_ctas": i.grid_ctas, "n_coop": i.n_coop, "regs_per_thread": i.regs_per_thread,
-            "resident_ctas_per_sm": i.resident_ctas_per_sm}
+            "resident_ctas_per_sm": i.resident_ctas_per_sm, "max_piece": i.max_piece,
+            "n_split_streams": i.n_split_streams, "n_jumps": i.n_jumps}
 
 
 class Server:

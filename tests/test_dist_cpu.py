@@ -106,7 +106,7 @@ def _bench_worker(rank, world, port, split, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         args = argparse.Namespace(workload="uneven", streams=0, count=0, param_sets=0, mexp=0,
-                                  split=split)
+                                  rank_split=split)
         w, desc = bench.rank_workload(args, rank, world)
         syncs = []
         with bench.bracket(dist, lambda: syncs.append(time.monotonic())):
