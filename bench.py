@@ -747,12 +747,18 @@ def measure_per_stream_launches(mtgp, torch, st, w, out, stream, flush):
             "how": "mtgp_generate_u32 once per stream, stream order, one CUDA stream"}
 
 
-# (label, workload, format) of the other configurations measured beside the
-# uneven headline: 4096 x 2^18 at Mexp 11213, and 1024 x 2^20 at Mexp 23209
-# and 44497 in the three output formats.
-EXTRA_CONFIGS = [("equal 4096 x 2^18, Mexp 11213, u32", "equal", "u32")] + [
-    ("long 1024 x 2^20, Mexp %d, %s" % (m, f), "long%d" % m, f)
-    for m in (23209, 44497) for f in ("u32", "f12", "f01")]
+# (label, workload, format, split, mexp) of the other configurations measured
+# beside the uneven headline: one stream of 2^20 numbers (unsplit, and in 64
+# pieces started by jumps), 4096 x 2^18 at Mexp 11213, 1024 x 2^20 at Mexp
+# 23209 and 44497 in the three output formats, and the uneven workload at
+# the paper's exponent 3217 (unsplit and split).
+EXTRA_CONFIGS = [("single stream x 2^20, Mexp 11213, u32", "single", "u32", "0", 0),
+                 ("single stream x 2^20, Mexp 11213, u32, 64 pieces", "single", "u32", "16384", 0),
+                 ("equal 4096 x 2^18, Mexp 11213, u32", "equal", "u32", "0", 0)] + [
+    ("long 1024 x 2^20, Mexp %d, %s" % (m, f), "long%d" % m, f, "0", 0)
+    for m in (23209, 44497) for f in ("u32", "f12", "f01")] + [
+    ("uneven 10 000 streams, Mexp 3217, u32", "uneven", "u32", "0", 3217),
+    ("uneven 10 000 streams, Mexp 3217, u32, split at 16 warps per SM", "uneven", "u32", "auto", 3217)]
 
 
 def measure_configs(mtgp, torch, dev, stream, flush, steps=5, warmup=3):
@@ -763,8 +769,9 @@ def measure_configs(mtgp, torch, dev, stream, flush, steps=5, warmup=3):
     peak, _ = hbm_peak()
     res = []
     buf = None
-    for label, name, fmt_name in EXTRA_CONFIGS:
-        w, desc = workload(name, 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    for label, name, fmt_name, split, mexp in EXTRA_CONFIGS:
+        w, desc = workload(name, 0, mexp=mexp)
         counts = w["counts"]
         total = int(counts.sum())
         if buf is None or buf.numel() < total:
@@ -775,6 +782,9 @@ def measure_configs(mtgp, torch, dev, stream, flush, steps=5, warmup=3):
         st = mtgp.mtgp_init_statuses(params, w["seeds"], stream)
         ids = np.arange(counts.size, dtype=np.uint32)
         plan = mtgp.mtgp_plan_create(st, ids, counts, fmt, out)
+        max_piece = split_piece(split, total, sms)
+        if max_piece:
+            mtgp.mtgp_plan_set_split(plan, max_piece)
         mtgp.mtgp_plan_autotune(plan)
         info = mtgp.mtgp_plan_get_info(plan)
         states0 = mtgp.mtgp_get_statuses(st, stream)
@@ -806,7 +816,8 @@ def measure_configs(mtgp, torch, dev, stream, flush, steps=5, warmup=3):
         res.append({"config": label, "workload": desc, "format": fmt_name, "numbers": total,
                     "gnum_s": total * steps / (t0.elapsed_time(t1) / 1e3) / 1e9,
                     "kernel_ms_avg": 1e3 * kern, "frac": alg / kern / 1e9 / peak,
-                    "launch": info["config"], "bit_exact_sample": exact})
+                    "launch": info["config"], "bit_exact_sample": exact,
+                    "split": {"max_piece": info["max_piece"], "jumps_per_launch": info["n_jumps"]}})
         del plan, st
     return res
 

@@ -279,6 +279,8 @@ typedef struct {
     uint64_t max_piece;       /* piece length of split streams (0 = no split)   */
     uint32_t n_split_streams; /* streams cut into pieces                        */
     uint32_t n_jumps;         /* jumps per launch (pieces after a first one)    */
+    uint32_t n_pieces;        /* pieces of the split streams                    */
+    uint32_t pad;
 } mtgp_plan_info;
 
 /* Sec. 1 and Sec. 2 (one generator's stream shared out as sub-streams;
@@ -286,15 +288,16 @@ typedef struct {
  * of the plan whose count exceeds max_piece into pieces of max_piece numbers
  * (the last one shorter; at most 64 pieces per stream, longer streams get 64
  * equal pieces), so that one long stream is advanced by several warps at
- * once.  Each launch then copies every split stream's state into a scratch
- * row per piece, advances the row of piece j by its offset j * max_piece
- * with an exact jump (mtgp_jump's method; its polynomials are computed here,
- * on the host, once per plan), and runs the generation kernel over the
- * pieces, longest first; the stream's last piece leaves the stream's new
- * state.  Outputs and states are exactly those of the unsplit plan.
- * max_piece = 0 removes the split; 1 .. 63 is MTGP_EINVAL.  Re-records the
- * plan's graph; synchronous.  The device scratch is one state row per
- * piece, held by the plan. */
+ * once.  A split plan runs on state rows of its own, one per launched item
+ * (a whole stream or a piece): each launch copies the streams' states into
+ * them, advances the rows of later pieces by their offsets j * max_piece
+ * with exact jumps (mtgp_jump's method; the jump polynomials are computed on
+ * the host once per plan), runs the generation kernel over the items,
+ * longest first, and copies the unsplit streams' rows and every split
+ * stream's last piece back as the streams' new states.  Outputs and states
+ * are exactly those of the unsplit plan.  max_piece = 0 removes the split;
+ * 1 .. 63 is MTGP_EINVAL.  Re-records the plan's graph; synchronous.  The
+ * plan holds N words of device memory per launched item. */
 mtgp_status mtgp_plan_set_split(mtgp_plan_t plan, uint64_t max_piece);
 
 /* Times the tuning candidates on this plan's own work table, on a scratch

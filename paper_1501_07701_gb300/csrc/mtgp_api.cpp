@@ -334,7 +334,7 @@ mtgp_status mtgp::build_work(uint32_t n_streams, const uint32_t* ids, const uint
         WorkItem it;
         it.stream = sid;
         it.seg_begin = (uint32_t)w.segs.size();
-        it.piece = 0;
+        it.pad = 0;
         uint64_t g = 0;
         while (i < order.size() && ids[order[i]] == sid) {
             const uint32_t j = order[i];
@@ -407,17 +407,28 @@ mtgp_status mtgp::split_work(const Work& w, uint64_t max_piece, uint32_t max_pie
         return MTGP_OK;
     }
     struct Piece {
-        WorkItem it;
+        WorkItem it;   // stream = the item's row
         uint64_t total;
         std::vector<Segment> segs;
     };
     std::vector<Piece> pieces;
+    auto new_row = [&](uint32_t stream) -> uint32_t {
+        const uint32_t row = o.n_rows++;
+        o.copies.push_back(make_uint2(stream, row));
+        o.row_set.push_back(set_of_stream.empty() ? 0u : set_of_stream[stream]);
+        return row;
+    };
     for (size_t i = 0; i < w.items.size(); ++i) {
         const WorkItem& it = w.items[i];
         const uint64_t T = w.item_total[i];
         const Segment* sg = w.segs.data() + it.seg_begin;
+        if (o.n_rows >= 0x7FFFFFF0u)
+            return fail(MTGP_EINVAL, "too many pieces");
         if (T <= max_piece) {
-            pieces.push_back(Piece{it, T, std::vector<Segment>(sg, sg + it.nseg)});
+            Piece p{it, T, std::vector<Segment>(sg, sg + it.nseg)};
+            p.it.stream = new_row(it.stream);
+            o.backs.push_back(make_uint2(p.it.stream, it.stream));
+            pieces.push_back(std::move(p));
             continue;
         }
         uint64_t L = max_piece;
@@ -427,22 +438,20 @@ mtgp_status mtgp::split_work(const Work& w, uint64_t max_piece, uint32_t max_pie
             k = (T + L - 1) / L;
         }
         ++o.n_split;
-        const uint32_t set = set_of_stream.empty() ? 0u : set_of_stream[it.stream];
+        o.n_pieces += (uint32_t)k;
         for (uint64_t j = 0; j < k; ++j) {
             const uint64_t lo = j * L, hi = std::min(T, lo + L);
-            if (o.n_scratch >= kPieceRow - 1u)
-                return fail(MTGP_EINVAL, "too many pieces");
-            const uint32_t row = o.n_scratch++;
-            o.copies.push_back(make_uint2(it.stream, row));
-            if (j > 0) {
-                o.jump_rows.push_back(row);
-                o.jump_sets.push_back(set);
-                o.jump_lens.push_back(lo);
-            }
             Piece p;
             p.it = it;
-            p.it.piece = (row + 1u) | (j + 1 == k ? kPieceLast : 0u);
+            p.it.stream = new_row(it.stream);
             p.total = hi - lo;
+            if (j > 0) {
+                o.jump_rows.push_back(p.it.stream);
+                o.jump_sets.push_back(o.row_set.back());
+                o.jump_lens.push_back(lo);
+            }
+            if (j + 1 == k)
+                o.backs.push_back(make_uint2(p.it.stream, it.stream));
             for (uint32_t q = 0; q < it.nseg; ++q) {
                 const uint64_t a = std::max(sg[q].g_start, lo);
                 const uint64_t b = std::min(sg[q].g_start + sg[q].count, hi);
@@ -758,19 +767,19 @@ mtgp_status mtgp::geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t 
 
 // Uploads a work table through the handle's slot ring and launches.
 mtgp_status mtgp::launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
-                              cudaStream_t s, uint32_t* scratch)
+                              cudaStream_t s)
 {
     if (w.items.empty())
         return MTGP_OK;
     TableSlot& sl = st->slots[st->next_slot];
     st->next_slot = (st->next_slot + 1) % (int)st->slots.size();
-    return launch_work_slot(st, sl, w, cfg, out, s, scratch);
+    return launch_work_slot(st, sl, w, cfg, out, s);
 }
 
 // Uploads a work table through `sl` (waiting for the slot's previous
 // consumer) and launches on `s`; records the slot's event after the kernel.
 mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w,
-                                   const LaunchCfg& cfg, void* out, cudaStream_t s, uint32_t* scratch)
+                                   const LaunchCfg& cfg, void* out, cudaStream_t s)
 {
     if (w.items.empty())
         return MTGP_OK;
@@ -814,7 +823,6 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
     a.trace = nullptr;
     a.sets = st->d_sets;
     a.set_of = st->d_set_of;
-    a.scratch = scratch;
     CUDA_TRY(launch_generate(a, g, s), "generation kernel launch");
     CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
     sl.ev_recorded = true;
@@ -1084,7 +1092,7 @@ std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
 
 // Times one configuration on scratch states: best of `reps` launches.
 mtgp_status mtgp::time_config(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, uint32_t* states,
-                              void* out, int reps, float* best_ms, uint32_t* scratch)
+                              void* out, int reps, float* best_ms)
 {
     cudaStream_t s = st->tune_stream;
     cudaEvent_t a = st->tune_ev[0], b = st->tune_ev[1];
@@ -1094,7 +1102,7 @@ mtgp_status mtgp::time_config(mtgp_streams* st, const Work& w, const LaunchCfg& 
     mtgp_status r = MTGP_OK;
     for (int i = 0; i < reps + 1 && r == MTGP_OK; ++i) {
         cudaEventRecord(a, s);
-        r = launch_work(st, w, cfg, out, s, scratch);
+        r = launch_work(st, w, cfg, out, s);
         cudaEventRecord(b, s);
         if (r != MTGP_OK)
             break;
@@ -1227,20 +1235,21 @@ static mtgp_status record_graph(mtgp_plan* p)
     cudaStream_t cap = p->cap_stream;
     const uint32_t n_copies = (uint32_t)p->split.copies.size();
     const uint32_t n_jumps = (uint32_t)p->jumps.items.size();
+    const bool split = p->split.n_rows > 0;
     CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    // split streams: every piece gets its stream's state, then the pieces
-    // after the first are jumped to their offsets
-    cudaError_t e1 = launch_copy_rows(p->st->d_states, p->d_scratch, p->d_copies, n_copies,
+    // split launches: every row gets its stream's state, then the rows of
+    // later pieces are jumped to their offsets
+    cudaError_t e1 = launch_copy_rows(p->st->d_states, p->d_rows, p->d_copies, n_copies,
                                       p->st->P.k.n, p->st->P.k.np, cap);
     if (e1 == cudaSuccess)
-        e1 = launch_jump_batch(p->st, p->d_scratch, p->d_jitems, n_jumps, p->d_jpolys, p->jumps.words,
+        e1 = launch_jump_batch(p->st, p->d_rows, p->d_jitems, n_jumps, p->d_jpolys, p->jumps.words,
                                p->jumps.smem, cap);
     if (e1 == cudaSuccess)
         e1 = cudaMemsetAsync(p->d_table, 0, 2 * sizeof(uint32_t), cap);
     GenArgs a;
     a.P = p->st->P.k;
-    a.states = p->st->d_states;
-    a.n_streams = p->st->n_streams;
+    a.states = split ? p->d_rows : p->st->d_states;
+    a.n_streams = split ? p->split.n_rows : p->st->n_streams;
     a.items = (const WorkItem*)((char*)p->d_table + p->items_off);
     a.segs = (const Segment*)((char*)p->d_table + p->segs_off);
     a.n_items = p->n_items;
@@ -1251,9 +1260,13 @@ static mtgp_status record_graph(mtgp_plan* p)
     a.err = p->st->d_err;
     a.trace = p->d_trace;
     a.sets = p->st->d_sets;
-    a.set_of = p->st->d_set_of;
-    a.scratch = p->d_scratch;
+    a.set_of = split ? p->d_row_set : p->st->d_set_of;
     cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, p->geo, cap) : e1;
+    // the streams' new states: unsplit streams' rows and split streams' last pieces
+    const uint32_t n_backs = (uint32_t)p->split.backs.size();
+    if (e2 == cudaSuccess)
+        e2 = launch_copy_rows(p->d_rows, p->st->d_states, p->d_backs, n_backs, p->st->P.k.n,
+                              p->st->P.k.np, cap);
     cudaGraph_t graph = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(cap, &graph);
     if (e2 != cudaSuccess) {
@@ -1265,7 +1278,7 @@ static mtgp_status record_graph(mtgp_plan* p)
         return fail_cuda(e3, "cudaStreamEndCapture");
     p->graph = graph;
     CUDA_TRY(cudaGraphInstantiate(&p->exec, graph, 0), "cudaGraphInstantiate");
-    p->kernel_launches = 1 + (n_copies ? 1u : 0u) + (n_jumps ? 1u : 0u);
+    p->kernel_launches = 1 + (n_copies ? 1u : 0u) + (n_jumps ? 1u : 0u) + (n_backs ? 1u : 0u);
     return MTGP_OK;
 }
 
@@ -1273,16 +1286,22 @@ static mtgp_status record_graph(mtgp_plan* p)
 // items and polynomials).
 static void free_split(mtgp_plan* p)
 {
-    if (p->d_scratch)
-        cudaFree(p->d_scratch);
+    if (p->d_rows)
+        cudaFree(p->d_rows);
     if (p->d_copies)
         cudaFree(p->d_copies);
+    if (p->d_backs)
+        cudaFree(p->d_backs);
+    if (p->d_row_set)
+        cudaFree(p->d_row_set);
     if (p->d_jitems)
         cudaFree(p->d_jitems);
     if (p->d_jpolys)
         cudaFree(p->d_jpolys);
-    p->d_scratch = nullptr;
+    p->d_rows = nullptr;
     p->d_copies = nullptr;
+    p->d_backs = nullptr;
+    p->d_row_set = nullptr;
     p->d_jitems = nullptr;
     p->d_jpolys = nullptr;
     p->jumps = JumpBatch();
@@ -1319,12 +1338,20 @@ static mtgp_status build_launch(mtgp_plan* p, uint64_t max_piece)
     fill_table(sw.work, host.data());
     CUDA_TRY(cudaMalloc(&p->d_table, bytes), "cudaMalloc(plan table)");
     CUDA_TRY(cudaMemcpy(p->d_table, host.data(), bytes, cudaMemcpyHostToDevice), "cudaMemcpy(plan table)");
-    if (sw.n_scratch) {
-        const size_t rows = (size_t)sw.n_scratch * st->P.k.np * 4;
-        CUDA_TRY(cudaMalloc(&p->d_scratch, rows), "cudaMalloc(piece states)");
+    if (sw.n_rows) {
+        const size_t rows = (size_t)sw.n_rows * st->P.k.np * 4;
+        CUDA_TRY(cudaMalloc(&p->d_rows, rows), "cudaMalloc(launch state rows)");
+        if (st->d_sets) {
+            CUDA_TRY(cudaMalloc(&p->d_row_set, sw.row_set.size() * 4), "cudaMalloc(row sets)");
+            CUDA_TRY(cudaMemcpy(p->d_row_set, sw.row_set.data(), sw.row_set.size() * 4,
+                                cudaMemcpyHostToDevice), "cudaMemcpy(row sets)");
+        }
         CUDA_TRY(cudaMalloc(&p->d_copies, sw.copies.size() * sizeof(uint2)), "cudaMalloc(copy pairs)");
         CUDA_TRY(cudaMemcpy(p->d_copies, sw.copies.data(), sw.copies.size() * sizeof(uint2),
                             cudaMemcpyHostToDevice), "cudaMemcpy(copy pairs)");
+        CUDA_TRY(cudaMalloc(&p->d_backs, sw.backs.size() * sizeof(uint2)), "cudaMalloc(copy-back pairs)");
+        CUDA_TRY(cudaMemcpy(p->d_backs, sw.backs.data(), sw.backs.size() * sizeof(uint2),
+                            cudaMemcpyHostToDevice), "cudaMemcpy(copy-back pairs)");
     }
     if (!jb.items.empty()) {
         CUDA_TRY(cudaMalloc(&p->d_jitems, jb.items.size() * sizeof(JumpItem)), "cudaMalloc(jump items)");
@@ -1450,7 +1477,18 @@ extern "C" mtgp_status mtgp_plan_autotune(mtgp_plan_t p, mtgp_launch_config* bes
             if (geometry_for(st, c, 1, &probe) != MTGP_OK)
                 continue;   // not launchable on this device (registers or shared memory)
             float ms = 0;
-            r = time_config(st, p->split.work, c, scratch, p->out, 2, &ms, p->d_scratch);
+            if (p->split.n_rows) {
+                // a split launch runs on the plan's own rows: time it there
+                const uint32_t ns = st->n_streams;
+                uint32_t* const so = st->d_set_of;
+                st->n_streams = p->split.n_rows;
+                st->d_set_of = st->d_sets ? p->d_row_set : so;
+                r = time_config(st, p->split.work, c, p->d_rows, p->out, 2, &ms);
+                st->n_streams = ns;
+                st->d_set_of = so;
+            } else {
+                r = time_config(st, p->split.work, c, scratch, p->out, 2, &ms);
+            }
             if (r != MTGP_OK) {
                 r = fail_candidate(r, c);
                 break;
@@ -1541,6 +1579,7 @@ extern "C" mtgp_status mtgp_plan_get_info(mtgp_plan_t p, mtgp_plan_info* info)
     info->n_items = p->n_items;
     info->max_piece = p->split.max_piece;
     info->n_split_streams = p->split.n_split;
+    info->n_pieces = p->split.n_pieces;
     info->n_jumps = (uint32_t)p->jumps.items.size();
     info->kernel_launches = p->kernel_launches;
     LaunchCfg eff = p->cfg;

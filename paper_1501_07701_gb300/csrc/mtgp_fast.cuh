@@ -316,8 +316,7 @@ __device__ __forceinline__ void gen_rows_pipelined(uint32_t (&r)[M], uint32_t* S
 // Advances one stream by the segments [s_begin, s_end) of the work table.
 // WG warps take part (WG = 1: this warp alone; WG = G: the whole CTA).
 template <int M, int K, int WG>
-__device__ __forceinline__ void run_item(const KParams& KP, const RowP& P, const uint32_t* __restrict__ g,
-                                         uint32_t* __restrict__ g_out,
+__device__ __forceinline__ void run_item(const KParams& KP, const RowP& P, uint32_t* __restrict__ g,
                                          uint32_t* __restrict__ S, const Segment* __restrict__ segs,
                                          uint32_t s_begin, uint32_t s_end, uint32_t* __restrict__ out,
                                          uint32_t warp, uint32_t lane, const uint32_t* __restrict__ Tb)
@@ -416,7 +415,7 @@ __device__ __forceinline__ void run_item(const KParams& KP, const RowP& P, const
     for (uint32_t j = tid; j < N; j += 32u * WG) {
         uint32_t c = phase + j;
         c = c >= N ? c - N : c;
-        g_out[j] = S[c];
+        g[j] = S[c];
     }
     if (WG > 1)
         __syncthreads();
@@ -438,8 +437,7 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
                                                            uint32_t* __restrict__ out, int* __restrict__ err,
                                                            uint64_t* __restrict__ trace,
                                                            const KSet* __restrict__ sets,
-                                                           const uint32_t* __restrict__ set_of,
-                                                           uint32_t* __restrict__ scratch)
+                                                           const uint32_t* __restrict__ set_of)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_claim;
@@ -477,10 +475,8 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
             continue;
         }
         const uint64_t t0 = trace ? global_ns() : 0;
-        uint32_t *g_in, *g_out;
-        item_rows(w, states, scratch, P.np, &g_in, &g_out);
-        run_item<M, K, G>(P, R0, g_in, g_out, smem, segs, w.seg_begin, w.seg_begin + w.nseg, out,
-                          warp, lane, Tb[0]);
+        run_item<M, K, G>(P, R0, states + (size_t)w.stream * P.np, smem, segs, w.seg_begin,
+                          w.seg_begin + w.nseg, out, warp, lane, Tb[0]);
         if (trace && threadIdx.x == 0)
             trace_item(trace, it, t0, segs, w);
     }
@@ -501,8 +497,6 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
             continue;
         }
         const uint64_t t0 = trace ? global_ns() : 0;
-        uint32_t *g_in, *g_out;
-        item_rows(w, states, scratch, P.np, &g_in, &g_out);
         if (sets) {
             // this stream's own parameter set
             const KSet& ks = sets[set_of[w.stream]];
@@ -513,11 +507,11 @@ __global__ void __launch_bounds__(G * 32) mtgp_fast_kernel(const KParams P, uint
                 Tb[warp][32u + lane] = ks.flt[lane];
             }
             __syncwarp();
-            run_item<M, K, 1>(P, R, g_in, g_out, S, segs, w.seg_begin, w.seg_begin + w.nseg, out,
-                              warp, lane, Tb[warp]);
+            run_item<M, K, 1>(P, R, states + (size_t)w.stream * P.np, S, segs, w.seg_begin,
+                              w.seg_begin + w.nseg, out, warp, lane, Tb[warp]);
         } else {
-            run_item<M, K, 1>(P, R0, g_in, g_out, S, segs, w.seg_begin, w.seg_begin + w.nseg, out,
-                              warp, lane, Tb[0]);
+            run_item<M, K, 1>(P, R0, states + (size_t)w.stream * P.np, S, segs, w.seg_begin,
+                              w.seg_begin + w.nseg, out, warp, lane, Tb[0]);
         }
         if (trace && lane == 0)
             trace_item(trace, it, t0, segs, w);

@@ -37,34 +37,15 @@ struct KSet {
 // One stream touched by a launch.  Its requests are the segments
 // [seg_begin, seg_begin + nseg); they are generated back to back, so the
 // stream's output index g runs over 0 .. total-1 across its segments.
-// piece = 0: the item starts from the stream's state row and leaves its end
-// state there.  A piece of a split stream instead starts from scratch state
-// row (piece & kPieceRow) - 1 (the stream's state jumped to the piece's
-// first number) and leaves its end state in that scratch row, or, with
-// kPieceLast set (the stream's last piece), in the stream's own row.
+// `stream` is the row of the launch's state array that the item advances:
+// the stream's own row, or, in a split launch, a row of the launch's own
+// array (see SplitWork).
 struct WorkItem {
     uint32_t stream;
     uint32_t seg_begin;
     uint32_t nseg;
-    uint32_t piece;
+    uint32_t pad;
 };
-constexpr uint32_t kPieceLast = 1u << 31;
-constexpr uint32_t kPieceRow = kPieceLast - 1u;
-
-// State rows an item reads and writes (see WorkItem).
-__host__ __device__ inline void item_rows(const WorkItem& w, uint32_t* states, uint32_t* scratch,
-                                          uint32_t np, uint32_t** in, uint32_t** out)
-{
-    uint32_t* own = states + (size_t)w.stream * np;
-    if (w.piece == 0u) {
-        *in = own;
-        *out = own;
-        return;
-    }
-    uint32_t* sr = scratch + (size_t)((w.piece & kPieceRow) - 1u) * np;
-    *in = sr;
-    *out = (w.piece & kPieceLast) ? own : sr;
-}
 
 // One request of a stream: numbers g in [g_start, g_start + count) of the
 // item go to out[out_off + (g - g_start)] in format fmt (0 u32, 1 f32 [1,2),
@@ -127,7 +108,6 @@ struct GenArgs {
     uint64_t* trace;     // optional: 4 words per item (start ns, end ns, SM, numbers)
     const KSet* sets = nullptr;        // per-stream parameter sets (null: every stream uses P)
     const uint32_t* set_of = nullptr;  // set index of each stream when `sets` is given
-    uint32_t* scratch = nullptr;       // scratch state rows of split streams' pieces
 };
 
 // Jump of one state row by a count J: row `stream` of the array given to the

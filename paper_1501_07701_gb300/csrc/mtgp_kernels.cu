@@ -72,8 +72,7 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
                                                         uint32_t n_items, uint32_t* __restrict__ counter,
                                                         uint32_t* __restrict__ out, int* __restrict__ err,
                                                         const KSet* __restrict__ sets,
-                                                        const uint32_t* __restrict__ set_of,
-                                                        uint32_t* __restrict__ scratch)
+                                                        const uint32_t* __restrict__ set_of)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
@@ -113,8 +112,7 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
             tmp[lane] = P.tmp[lane];
         }
         const uint32_t Wc = (N - pos) < 32u ? (N - pos) : 32u;
-        uint32_t *g, *g_out;
-        item_rows(w, states, scratch, P.np, &g, &g_out);
+        uint32_t* g = states + (size_t)w.stream * P.np;
         for (uint32_t j = lane; j < N; j += 32u)
             S[j] = g[j];
         __syncwarp();
@@ -168,7 +166,7 @@ __global__ void __launch_bounds__(256) mtgp_ring_kernel(const KParams P, uint32_
         for (uint32_t j = lane; j < N; j += 32u) {
             uint32_t c = phase + j;
             c = c >= N ? c - N : c;
-            g_out[j] = S[c];
+            g[j] = S[c];
         }
         __syncwarp();
     }
@@ -302,7 +300,7 @@ cudaError_t launch_generate(const GenArgs& a, const Geometry& g, cudaStream_t s)
                            dim3(g.threads), g.smem, s);
     mtgp_ring_kernel<<<g.grid, g.threads, g.smem, s>>>(a.P, a.states, a.n_streams, a.items, a.segs,
                                                        a.n_items, a.counter, a.out, a.err, a.sets,
-                                                       a.set_of, a.scratch);
+                                                       a.set_of);
     return cudaGetLastError();
 }
 
@@ -352,9 +350,8 @@ cudaError_t launch_gen_fn(const void* fn, const GenArgs& a, dim3 grid, dim3 bloc
     uint64_t* trace = a.trace;
     const KSet* sets = a.sets;
     const uint32_t* set_of = a.set_of;
-    uint32_t* scratch = a.scratch;
     void* args[] = {&P, &states, &n_streams, &items, &segs, &n_items, &n_coop, &counter, &out, &err,
-                    &trace, &sets, &set_of, &scratch};
+                    &trace, &sets, &set_of};
     return cudaLaunchKernel(fn, grid, block, args, smem, s);
 }
 

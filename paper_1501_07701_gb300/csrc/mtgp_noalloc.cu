@@ -147,7 +147,7 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
         WorkItem it;
         it.stream = ids[j];
         it.seg_begin = n_segs;
-        it.piece = 0;
+        it.pad = 0;
         uint64_t g = 0, off = 0;
         for (uint32_t k = 0; k < n_req; ++k) {
             if (ids[k] == ids[j] && counts[k] != 0) {

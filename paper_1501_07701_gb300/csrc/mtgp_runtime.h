@@ -104,17 +104,24 @@ struct JumpBatch {
     size_t smem = 0;
 };
 
-// A launch whose longest streams are cut into pieces: `work` holds the
-// pieces as items (see WorkItem::piece); before the generation kernel,
-// `copies` (stream row -> scratch row) give every piece its stream's state
-// and `jumps` advance the scratch rows of pieces after the first by the
-// piece's offset in the stream.
+// A launch whose longest streams are cut into pieces.  It runs the
+// generation kernel on a state array of its own with one row per launched
+// item (a whole stream, or one piece): `work` holds the items with their
+// rows in WorkItem::stream.  Before the kernel, `copies` (stream -> row)
+// give every row its stream's state and `jumps` advance the rows of pieces
+// after a stream's first by the piece's offset in the stream; after it,
+// `backs` (row -> stream) return the state of every unsplit stream and of
+// every split stream's last piece.  row_set: parameter-set index of each
+// row's stream (handles with one set per stream).
 struct SplitWork {
     Work work;
     uint64_t max_piece = 0;        // 0 = not split
-    uint32_t n_scratch = 0;        // scratch state rows
+    uint32_t n_rows = 0;           // rows of the launch's own state array
     uint32_t n_split = 0;          // streams cut into pieces
+    uint32_t n_pieces = 0;         // pieces of those streams
     std::vector<uint2> copies;
+    std::vector<uint2> backs;
+    std::vector<uint32_t> row_set;
     std::vector<uint32_t> jump_rows, jump_sets;
     std::vector<uint64_t> jump_lens;
 };
@@ -132,9 +139,12 @@ struct mtgp_plan {
     mtgp::Geometry geo{};
     mtgp::Work work;               // the requests, one item per stream
     mtgp::SplitWork split;         // the launched work (pieces when split)
-    // split launches: scratch rows, copy pairs, jump items and polynomials
-    uint32_t* d_scratch = nullptr;
+    // split launches: the launch's state rows, copy pairs, per-row parameter
+    // set index, jump items and polynomials
+    uint32_t* d_rows = nullptr;
     uint2* d_copies = nullptr;
+    uint2* d_backs = nullptr;
+    uint32_t* d_row_set = nullptr;
     mtgp::JumpItem* d_jitems = nullptr;
     uint32_t* d_jpolys = nullptr;
     mtgp::JumpBatch jumps;
@@ -160,22 +170,22 @@ void fill_table(const Work& w, void* host);
 LaunchCfg default_config(const KParams& P);
 mtgp_status geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t n_items, Geometry* g);
 mtgp_status launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
-                        cudaStream_t s, uint32_t* scratch = nullptr);
+                        cudaStream_t s);
 mtgp_status launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w, const LaunchCfg& cfg,
-                             void* out, cudaStream_t s, uint32_t* scratch = nullptr);
+                             void* out, cudaStream_t s);
 void free_table_slot(TableSlot& s);
 mtgp_status validate_config(const mtgp_launch_config* c, LaunchCfg* out);
 // Number of leading (longest) items a launch hands to whole CTAs.
 uint32_t coop_count(const Work& w, const Geometry& g, int coop_percent);
 std::vector<LaunchCfg> tuning_candidates(const KParams& P);
 mtgp_status time_config(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, uint32_t* states,
-                        void* out, int reps, float* best_ms, uint32_t* scratch = nullptr);
+                        void* out, int reps, float* best_ms);
 
 // Cuts the items of `w` longer than max_piece numbers into pieces of
 // max_piece numbers (the last one shorter), at most max_pieces per stream
-// (longer streams get equal pieces of ceil(total / max_pieces)), and sorts
-// all items longest first.  set_of_stream: per-stream parameter set index
-// (empty for one shared set).
+// (longer streams get equal pieces of ceil(total / max_pieces)), gives every
+// item its own row, and sorts the items longest first.  set_of_stream:
+// per-stream parameter set index (empty for one shared set).
 mtgp_status split_work(const Work& w, uint64_t max_piece, uint32_t max_pieces,
                        const std::vector<uint32_t>& set_of_stream, SplitWork* out);
 

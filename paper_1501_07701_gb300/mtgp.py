@@ -53,7 +53,7 @@ class PlanInfo(ctypes.Structure):
                 ("grid_ctas", ctypes.c_uint32), ("n_coop", ctypes.c_uint32),
                 ("regs_per_thread", ctypes.c_uint32), ("resident_ctas_per_sm", ctypes.c_uint32),
                 ("max_piece", ctypes.c_uint64), ("n_split_streams", ctypes.c_uint32),
-                ("n_jumps", ctypes.c_uint32)]
+                ("n_jumps", ctypes.c_uint32), ("n_pieces", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class MtParams(ctypes.Structure):
@@ -465,7 +465,7 @@ def mtgp_plan_get_info(plan: Plan) -> dict:
             "kernel_launches": i.kernel_launches, "config": i.config.as_dict(),
             "grid_ctas": i.grid_ctas, "n_coop": i.n_coop, "regs_per_thread": i.regs_per_thread,
             "resident_ctas_per_sm": i.resident_ctas_per_sm, "max_piece": i.max_piece,
-            "n_split_streams": i.n_split_streams, "n_jumps": i.n_jumps}
+            "n_split_streams": i.n_split_streams, "n_jumps": i.n_jumps, "n_pieces": i.n_pieces}
 
 
 class Server:

@@ -144,7 +144,7 @@ def test_split_with_autotune_and_trace():
     mtgp.mtgp_plan_autotune(plan)
     mtgp.mtgp_plan_set_trace(plan, True)
     info = mtgp.mtgp_plan_get_info(plan)
-    assert info["n_split_streams"] > 0 and info["kernel_launches"] == 3
+    assert info["n_split_streams"] > 0 and info["kernel_launches"] == 4
     mtgp.mtgp_plan_launch(plan)
     torch.cuda.synchronize()
     ref, states = oracle.generate_many(op, states, ids, counts, 0, THREADS)
