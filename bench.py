@@ -376,6 +376,8 @@ def run_ours(args, rank, world, local_rank):
     qual = None
     if rank == 0 and args.quality:
         qual = quality_stats(mtgp, torch, out, counts, stream)
+        qual["fused"] = measure_fused_stats(mtgp, torch, st, ids, counts, out, stream, flush,
+                                            total / kern_avg / 1e9)
 
     # self-measured write-only bandwidth (fill of the output buffer)
     wb_a, wb_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -495,6 +497,48 @@ def quality_stats(mtgp, torch, out, counts, stream):
                          "gnum_s": total / (q0.elapsed_time(q1) * 1e6), "pooled": g},
             "hamming_indep": {"r": 25, "s": 5, "L": 1200, "classes": len(bounds) + 1,
                               "gnum_s": total / (q1.elapsed_time(q2) * 1e6), "pooled": hm}}
+
+
+def measure_fused_stats(mtgp, torch, st, ids, counts, out, stream, flush, gen_rate, steps=5):
+    """Generation with both statistics fused in (mtgp_plan_set_stats, the
+    parameters of quality_stats): per-launch rate over `steps` launches
+    (CUDA events, the L2 rewrite between launches as in the timed region),
+    next to generation alone timed the same way; the fused counts of the last
+    launch are compared with the standalone reductions over its output."""
+    from paper_1501_07701_gb300 import quality
+    bounds = quality.default_hamming_bounds(1200, 4)
+    total = int(counts.sum())
+    plan = mtgp.mtgp_plan_create(st, ids, counts, FORMATS["u32"], out)
+    try:
+        mtgp.mtgp_plan_set_stats(plan, gap=(25, 5, 128), hamming=(25, 5, 1200, bounds))
+    except mtgp.MtgpError as e:
+        return {"unavailable": str(e)}
+    info = mtgp.mtgp_plan_get_info(plan)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            mtgp.mtgp_plan_launch(plan, stream)
+            flush.fill_(2)
+        for i in range(steps):
+            ev[i][0].record(stream)
+            mtgp.mtgp_plan_launch(plan, stream)
+            ev[i][1].record(stream)
+            flush.fill_(i)
+    stream.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    hist, tab = mtgp.mtgp_plan_read_stats(plan, stream)
+    sh = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128, stream=stream)
+    stab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds, stream=stream)
+    rate = total / (sum(ms) / len(ms) / 1e3) / 1e9
+    return {"gnum_s": rate, "generation_alone_gnum_s": gen_rate, "ratio": rate / gen_rate,
+            "kernel_ms": [round(v, 3) for v in ms], "steps": steps,
+            "kernel": "mtgp_fused_kernel", "launch": info["config"], "grid_ctas": info["grid_ctas"],
+            "regs_per_thread": info["regs_per_thread"],
+            "resident_ctas_per_sm": info["resident_ctas_per_sm"],
+            "counts_equal_standalone": bool(np.array_equal(hist, sh) and np.array_equal(tab, stab)),
+            "pooled_gap": quality.gap_test(hist.sum(axis=0), b=5),
+            "pooled_hamming": quality.hamming_test(tab.sum(axis=0), L=1200, bounds=bounds)}
 
 
 def run_mt(args, rank, world, local_rank):

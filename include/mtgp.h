@@ -280,7 +280,7 @@ typedef struct {
     uint32_t n_split_streams; /* streams cut into pieces                        */
     uint32_t n_jumps;         /* jumps per launch (pieces after a first one)    */
     uint32_t n_pieces;        /* pieces of the split streams                    */
-    uint32_t pad;
+    uint32_t stats;           /* 1: statistics fused into generation            */
 } mtgp_plan_info;
 
 /* Sec. 1 and Sec. 2 (one generator's stream shared out as sub-streams;
@@ -299,6 +299,44 @@ typedef struct {
  * 1 .. 63 is MTGP_EINVAL.  Re-records the plan's graph; synchronous.  The
  * plan holds N words of device memory per launched item. */
 mtgp_status mtgp_plan_set_split(mtgp_plan_t plan, uint64_t max_piece);
+
+/* Configuration of the statistics fused into a plan (mtgp_plan_set_stats):
+ * the data reductions of the paper's two failing BigCrush tests (Sec. 4.2)
+ * with the parameters and definitions of mtgp_gap_histogram and
+ * mtgp_hamming_pairs.  gap_t = 0 leaves out the gap test; ham_L = 0 leaves
+ * out the Hamming test. */
+typedef struct {
+    uint32_t gap_r, gap_b, gap_t;   /* test 35: b >= 1, r + b <= 32, 1 <= t <= 1023      */
+    uint32_t ham_r, ham_s, ham_L;   /* test 100: s >= 1, r + s <= 32, L % s == 0, L/s >= 32 */
+    uint32_t n_bounds;              /* weight classes C = n_bounds + 1 <= 16              */
+    uint32_t bounds[15];            /* ascending class bounds (first n_bounds used)       */
+} mtgp_stats_config;
+
+/* Sec. 4.2 (the gap test, test 35, and Hamming-weight independence,
+ * test 100): makes every later launch of the plan also compute, for each of
+ * its requests, the gap histogram and the Hamming block-pair table of the
+ * 32-bit words it stores (the tempered outputs, or the float bit patterns
+ * of a float format), exactly as mtgp_gap_histogram and mtgp_hamming_pairs
+ * would over the plan's output buffer, request j being sequence j.  The
+ * counts are accumulated by a generation kernel of its own while the
+ * outputs are still in registers, so the outputs are not read back from
+ * memory; mtgp_plan_read_stats returns them.  cfg = NULL (or both tests
+ * left out) returns the plan to the plain generation kernel.
+ * MTGP_EINVAL: parameters out of range; a split plan or one with tracing
+ * on; a request of 2^32 numbers or more; a parameter set with N - pos < 256
+ * or a state size without an instantiation of the fused kernel (the
+ * exponents whose ceil(N/32) is 10, 11, 20, 22, 23 or 44, e.g. 11213, 23209
+ * and 44497).  Re-records the plan's graph; synchronous.  No counterpart in
+ * the paper beyond the tests' definitions: it fuses the paper's quality
+ * measurements into generation. */
+mtgp_status mtgp_plan_set_stats(mtgp_plan_t plan, const mtgp_stats_config* cfg);
+
+/* Copies the statistics of the plan's last launch (queued on cuda_stream)
+ * to the host: hist (n_req x (gap_t + 1), may be NULL when the gap test is
+ * off) and table (n_req x C x C, may be NULL when the Hamming test is off),
+ * in the layouts of mtgp_gap_histogram and mtgp_hamming_pairs.  Waits for
+ * cuda_stream.  MTGP_EINVAL when the plan has no statistics. */
+mtgp_status mtgp_plan_read_stats(mtgp_plan_t plan, uint64_t* hist, uint64_t* table, void* cuda_stream);
 
 /* Times the tuning candidates on this plan's own work table, on a scratch
  * copy of all states (the handle's states are not advanced; the plan's `out`

@@ -343,7 +343,7 @@ mtgp_status mtgp::build_work(uint32_t n_streams, const uint32_t* ids, const uint
             s.count = counts[j];
             s.out_off = off[j];
             s.fmt = fmts ? (uint32_t)fmts[j] : fmt_all;
-            s.pad = 0;
+            s.req = j;
             w.segs.push_back(s);
             g += counts[j];
             ++i;
@@ -1261,7 +1261,21 @@ static mtgp_status record_graph(mtgp_plan* p)
     a.trace = p->d_trace;
     a.sets = p->st->d_sets;
     a.set_of = split ? p->d_row_set : p->st->d_set_of;
-    cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, p->geo, cap) : e1;
+    cudaError_t e2 = e1;
+    if (e2 == cudaSuccess && p->stats) {
+        // the fused kernel writes every request's counts; requests with no
+        // numbers keep the zeros of these memsets
+        a.n_coop = p->n_coop = 0;
+        e2 = p->sa.hist ? cudaMemsetAsync(p->sa.hist, 0, (size_t)p->n_req * (p->sa.t + 1u) * 8u, cap)
+                        : cudaSuccess;
+        if (e2 == cudaSuccess && p->sa.tab)
+            e2 = cudaMemsetAsync(p->sa.tab, 0, (size_t)p->n_req * p->sa.C * p->sa.C * 8u, cap);
+        if (e2 == cudaSuccess)
+            e2 = launch_fused(p->stats_fn, a, p->sa, dim3(p->stats_geo.grid), dim3(p->stats_geo.threads),
+                              p->stats_geo.smem, cap);
+    } else if (e2 == cudaSuccess) {
+        e2 = launch_generate(a, p->geo, cap);
+    }
     // the streams' new states: unsplit streams' rows and split streams' last pieces
     const uint32_t n_backs = (uint32_t)p->split.backs.size();
     if (e2 == cudaSuccess)
@@ -1374,6 +1388,50 @@ static mtgp_status build_launch(mtgp_plan* p, uint64_t max_piece)
     return geometry_for(st, p->cfg, p->n_items, &p->geo);
 }
 
+// Kernel and launch geometry of a plan's fused statistics: G = 8 warps per
+// CTA, as many resident CTAs per SM as the plan's configuration asks warps
+// per SM (warps_per_cta x ctas_per_sm / 8, at least 1; occupancy maximum when
+// ctas_per_sm is 0), persistent grid.  The kernel takes single-warp items
+// with 128-word pipelined steps, so every parameter set needs N - pos >= 256
+// (the handle's representative set has the largest pos of its sets).
+static mtgp_status stats_geometry(mtgp_plan* p)
+{
+    mtgp_streams* st = p->st;
+    const KParams& P = st->P.k;
+    const int G = 8;
+    const int M = (int)((P.n + 31u) / 32u);
+    const void* fn = fused_kernel_ptr(M, G);
+    if (!fn)
+        return fail(MTGP_EINVAL, "statistics: no fused kernel for N = %u (ceil(N/32) = %d)", P.n, M);
+    if (P.n - P.pos < 256u)
+        return fail(MTGP_EINVAL, "statistics: N - pos = %u below 256", P.n - P.pos);
+    Geometry g{};
+    g.kernel = 0;
+    g.k = 4;
+    g.threads = G * 32;
+    g.smem = (size_t)G * (fast_smem_words(P.n, P.mirror) + stats_smem_words(p->sa.t, p->sa.C)) * 4u;
+    if (g.smem > 48u * 1024u)
+        CUDA_TRY(allow_max_dynamic_smem(fn, st->device, g.smem), "statistics kernel shared memory");
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem),
+             "statistics kernel occupancy");
+    if (per_sm < 1)
+        return fail(MTGP_EINVAL, "statistics kernel does not fit on an SM");
+    if (p->cfg.ctas_per_sm > 0)
+        per_sm = std::min(per_sm, std::max(1, p->cfg.warps_per_cta * p->cfg.ctas_per_sm / G));
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, fn), "cudaFuncGetAttributes");
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, st->device), "SM count");
+    g.regs = fa.numRegs;
+    g.per_sm = per_sm;
+    const long long want = ((long long)p->n_items + G - 1) / G;
+    g.grid = (int)std::max(1LL, std::min(want, (long long)sms * per_sm));
+    p->stats_fn = fn;
+    p->stats_geo = g;
+    return MTGP_OK;
+}
+
 static void destroy_plan(mtgp_plan* p)
 {
     if (!p)
@@ -1389,6 +1447,10 @@ static void destroy_plan(mtgp_plan* p)
         cudaFree(p->d_table);
     if (p->d_trace)
         cudaFree(p->d_trace);
+    if (p->d_hist)
+        cudaFree(p->d_hist);
+    if (p->d_tab)
+        cudaFree(p->d_tab);
     free_split(p);
     delete p;
 }
@@ -1416,6 +1478,7 @@ extern "C" mtgp_status mtgp_plan_create(mtgp_streams_t st, const uint32_t* ids, 
     p->max_item = w.max_item;
     p->cfg = st->cfg;
     p->work = w;
+    p->n_req = n_req;
     auto bail = [&](mtgp_status r) {
         destroy_plan(p);
         return r;
@@ -1507,6 +1570,8 @@ extern "C" mtgp_status mtgp_plan_autotune(mtgp_plan_t p, mtgp_launch_config* bes
     r = geometry_for(st, p->cfg, p->n_items, &p->geo);
     if (r != MTGP_OK)
         return r;
+    if (p->stats && (r = stats_geometry(p)) != MTGP_OK)
+        return r;
     r = record_graph(p);
     if (r != MTGP_OK)
         return r;
@@ -1521,6 +1586,8 @@ extern "C" mtgp_status mtgp_plan_set_trace(mtgp_plan_t p, int enable)
     GUARD_BEGIN
     if (!p)
         return fail(MTGP_EINVAL, "null plan");
+    if (enable && p->stats)
+        return fail(MTGP_EINVAL, "the plan computes statistics: its kernel keeps no timeline");
     DeviceGuard g(p->st->device);
     CUDA_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     if (enable && !p->d_trace && p->n_items) {
@@ -1560,6 +1627,8 @@ extern "C" mtgp_status mtgp_plan_set_split(mtgp_plan_t p, uint64_t max_piece)
         return fail(MTGP_EINVAL, "null plan");
     if (max_piece != 0 && max_piece < 64)
         return fail(MTGP_EINVAL, "max_piece %llu below 64", (unsigned long long)max_piece);
+    if (max_piece != 0 && p->stats)
+        return fail(MTGP_EINVAL, "the plan computes statistics per request: its requests cannot be split");
     DeviceGuard g(p->st->device);
     mtgp_status r = build_launch(p, max_piece);
     if (r != MTGP_OK)
@@ -1567,6 +1636,103 @@ extern "C" mtgp_status mtgp_plan_set_split(mtgp_plan_t p, uint64_t max_piece)
     r = record_graph(p);
     if (r != MTGP_OK)
         return r;
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_plan_set_stats(mtgp_plan_t p, const mtgp_stats_config* c)
+{
+    GUARD_BEGIN
+    if (!p)
+        return fail(MTGP_EINVAL, "null plan");
+    const bool gap = c && c->gap_t != 0;
+    const bool ham = c && c->ham_L != 0;
+    StatsArgs a{};
+    a.C = 1;
+    if (gap) {
+        if (c->gap_b < 1 || c->gap_r + c->gap_b > 32 || c->gap_t > 1023)
+            return fail(MTGP_EINVAL, "gap test: need b >= 1, r + b <= 32, 1 <= t <= 1023 (r %u b %u t %u)",
+                        c->gap_r, c->gap_b, c->gap_t);
+        a.gmask = (uint32_t)((((uint64_t)1 << c->gap_b) - 1u) << (32u - c->gap_r - c->gap_b));
+        a.t = c->gap_t;
+    }
+    if (ham) {
+        if (c->ham_s < 1 || c->ham_r + c->ham_s > 32 || c->ham_L % c->ham_s != 0 ||
+            c->ham_L / c->ham_s < 32 || c->n_bounds > 15)
+            return fail(MTGP_EINVAL, "Hamming test: need s >= 1, r + s <= 32, L a multiple of s with "
+                        "L/s >= 32, at most 15 bounds (r %u s %u L %u bounds %u)",
+                        c->ham_r, c->ham_s, c->ham_L, c->n_bounds);
+        a.hmask = (uint32_t)((((uint64_t)1 << c->ham_s) - 1u) << (32u - c->ham_r - c->ham_s));
+        a.K = c->ham_L / c->ham_s;
+        a.C = c->n_bounds + 1u;
+        for (uint32_t i = 0; i < c->n_bounds; ++i)
+            a.bounds[i] = c->bounds[i];
+    }
+    if ((gap || ham) && p->split.max_piece)
+        return fail(MTGP_EINVAL, "statistics per request need an unsplit plan");
+    if ((gap || ham) && p->d_trace)
+        return fail(MTGP_EINVAL, "statistics: turn the plan's trace off first");
+    if (gap || ham)
+        for (const Segment& sg : p->work.segs)
+            if (sg.count >> 32)
+                return fail(MTGP_EINVAL, "statistics: request %u has 2^32 or more numbers", sg.req);
+    DeviceGuard g(p->st->device);
+    CUDA_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    const bool was = p->stats;
+    const StatsArgs old = p->sa;
+    p->stats = false;
+    if (gap || ham) {
+        p->sa = a;
+        p->stats = true;
+        mtgp_status r = stats_geometry(p);
+        if (r != MTGP_OK) {
+            p->stats = was;
+            p->sa = old;
+            return r;
+        }
+    }
+    if (p->d_hist)
+        cudaFree(p->d_hist);
+    if (p->d_tab)
+        cudaFree(p->d_tab);
+    p->d_hist = nullptr;
+    p->d_tab = nullptr;
+    if (p->stats) {
+        const size_t nr = std::max<uint32_t>(p->n_req, 1u);
+        if (gap)
+            CUDA_TRY(cudaMalloc(&p->d_hist, nr * (a.t + 1u) * 8u), "cudaMalloc(gap histograms)");
+        if (ham)
+            CUDA_TRY(cudaMalloc(&p->d_tab, nr * a.C * a.C * 8u), "cudaMalloc(Hamming tables)");
+        p->sa.hist = p->d_hist;
+        p->sa.tab = p->d_tab;
+    } else {
+        p->sa = StatsArgs{};
+    }
+    mtgp_status r = record_graph(p);
+    if (r != MTGP_OK)
+        return r;
+    return ok();
+    GUARD_END
+}
+
+extern "C" mtgp_status mtgp_plan_read_stats(mtgp_plan_t p, uint64_t* hist, uint64_t* table, void* cuda_stream)
+{
+    GUARD_BEGIN
+    if (!p)
+        return fail(MTGP_EINVAL, "null plan");
+    if (!p->stats)
+        return fail(MTGP_EINVAL, "the plan computes no statistics");
+    if ((p->d_hist && !hist && p->n_req) || (p->d_tab && !table && p->n_req))
+        return fail(MTGP_EINVAL, "null output array for a test the plan computes");
+    DeviceGuard g(p->st->device);
+    cudaStream_t cs = (cudaStream_t)cuda_stream;
+    if (p->d_hist && p->n_req)
+        CUDA_TRY(cudaMemcpyAsync(hist, p->d_hist, (size_t)p->n_req * (p->sa.t + 1u) * 8u,
+                                 cudaMemcpyDeviceToHost, cs), "cudaMemcpyAsync(gap histograms)");
+    if (p->d_tab && p->n_req)
+        CUDA_TRY(cudaMemcpyAsync(table, p->d_tab, (size_t)p->n_req * p->sa.C * p->sa.C * 8u,
+                                 cudaMemcpyDeviceToHost, cs), "cudaMemcpyAsync(Hamming tables)");
+    CUDA_TRY(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
     return ok();
     GUARD_END
 }
@@ -1582,14 +1748,17 @@ extern "C" mtgp_status mtgp_plan_get_info(mtgp_plan_t p, mtgp_plan_info* info)
     info->n_pieces = p->split.n_pieces;
     info->n_jumps = (uint32_t)p->jumps.items.size();
     info->kernel_launches = p->kernel_launches;
+    const Geometry& geo = p->stats ? p->stats_geo : p->geo;
     LaunchCfg eff = p->cfg;
-    eff.kernel = p->geo.kernel;
-    eff.k = p->geo.k;
+    eff.kernel = geo.kernel;
+    eff.k = geo.k;
+    eff.warps_per_cta = geo.threads / 32;
     info->config = to_public(eff);
-    info->grid_ctas = (uint32_t)p->geo.grid;
+    info->grid_ctas = (uint32_t)geo.grid;
     info->n_coop = p->n_coop;
-    info->regs_per_thread = (uint32_t)p->geo.regs;
-    info->resident_ctas_per_sm = (uint32_t)p->geo.per_sm;
+    info->regs_per_thread = (uint32_t)geo.regs;
+    info->resident_ctas_per_sm = (uint32_t)geo.per_sm;
+    info->stats = p->stats ? 1u : 0u;
     return ok();
 }
 

@@ -49,13 +49,13 @@ struct WorkItem {
 
 // One request of a stream: numbers g in [g_start, g_start + count) of the
 // item go to out[out_off + (g - g_start)] in format fmt (0 u32, 1 f32 [1,2),
-// 2 f32 [0,1)).
+// 2 f32 [0,1)); req = the request's index in the call (its statistics row).
 struct Segment {
     uint64_t g_start;
     uint64_t count;
     uint64_t out_off;
     uint32_t fmt;
-    uint32_t pad;
+    uint32_t req;
 };
 
 struct LaunchCfg {
@@ -155,5 +155,34 @@ const void* fast_kernel_ptr(int M, int K, int G);
 // Launches a generation kernel with the register-resident kernel's signature.
 cudaError_t launch_gen_fn(const void* fn, const GenArgs& a, dim3 grid, dim3 block, size_t smem,
                           cudaStream_t s);
+
+// Statistics of the paper's gap test (test 35) and Hamming-weight
+// independence test (test 100), Sec. 4.2, accumulated by the fused
+// generation kernel per request of its launch.
+struct StatsArgs {
+    uint32_t gmask;                // gap test: the b bits after r dropped leading bits (0: off)
+    uint32_t t;                    // gap lengths >= t pooled in class t (t + 1 counts)
+    uint32_t hmask;                // Hamming test: the s bits after r dropped leading bits (0: off)
+    uint32_t K;                    // values per L-bit block (L / s), >= 32
+    uint32_t C;                    // weight classes (n_bounds + 1), <= 16
+    uint32_t bounds[15];           // class of weight w = number of bounds <= w
+    unsigned long long* hist;      // n_req x (t + 1) counts
+    unsigned long long* tab;       // n_req x C x C counts
+};
+
+// Shared-memory words per warp that the statistics add: the histogram and
+// the table of the warp's current request, each rounded up to 4 words.
+__host__ __device__ inline uint32_t stats_smem_words(uint32_t t, uint32_t C)
+{
+    return ((t + 1u + 3u) & ~3u) + ((C * C + 3u) & ~3u);
+}
+
+// The fused generation kernel (single-warp items, 128-word pipelined steps,
+// N - pos >= 256 for every parameter set): null when M or G has no
+// instantiation.  Launched like the register-resident kernel plus `A`
+// (a.n_coop and a.trace are not used).
+const void* fused_kernel_ptr(int M, int G);
+cudaError_t launch_fused(const void* fn, const GenArgs& a, const StatsArgs& A, dim3 grid, dim3 block,
+                         size_t smem, cudaStream_t s);
 
 }  // namespace mtgp

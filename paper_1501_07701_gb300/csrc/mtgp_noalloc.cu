@@ -156,7 +156,7 @@ extern "C" mtgp_status mtgp_generate_noalloc(mtgp_streams_t st, const uint32_t* 
                 s.count = counts[k];
                 s.out_off = off;
                 s.fmt = (uint32_t)fmt;
-                s.pad = 0;
+                s.req = k;
                 g += counts[k];
             }
             off += counts[k];

@@ -155,6 +155,15 @@ struct mtgp_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint32_t kernel_launches = 0;
+    uint32_t n_req = 0;            // requests of the plan (statistics rows)
+    // fused statistics (mtgp_plan_set_stats): the kernel, its geometry and
+    // arguments, and the per-request counts it writes
+    bool stats = false;
+    mtgp::StatsArgs sa{};
+    const void* stats_fn = nullptr;
+    mtgp::Geometry stats_geo{};
+    unsigned long long* d_hist = nullptr;
+    unsigned long long* d_tab = nullptr;
 };
 
 namespace mtgp {

@@ -53,7 +53,13 @@ class PlanInfo(ctypes.Structure):
                 ("grid_ctas", ctypes.c_uint32), ("n_coop", ctypes.c_uint32),
                 ("regs_per_thread", ctypes.c_uint32), ("resident_ctas_per_sm", ctypes.c_uint32),
                 ("max_piece", ctypes.c_uint64), ("n_split_streams", ctypes.c_uint32),
-                ("n_jumps", ctypes.c_uint32), ("n_pieces", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("n_jumps", ctypes.c_uint32), ("n_pieces", ctypes.c_uint32), ("stats", ctypes.c_uint32)]
+
+
+class StatsConfig(ctypes.Structure):
+    """mtgp_stats_config (include/mtgp.h)."""
+    _fields_ = [(f, ctypes.c_uint32) for f in ("gap_r", "gap_b", "gap_t", "ham_r", "ham_s", "ham_L",
+                                                "n_bounds")] + [("bounds", ctypes.c_uint32 * 15)]
 
 
 class MtParams(ctypes.Structure):
@@ -120,6 +126,8 @@ _SIGS = {
                          ctypes.POINTER(_VP)],
     "mtgp_plan_launch": [_VP, _VP],
     "mtgp_plan_set_split": [_VP, ctypes.c_uint64],
+    "mtgp_plan_set_stats": [_VP, ctypes.POINTER(StatsConfig)],
+    "mtgp_plan_read_stats": [_VP, _U64P, _U64P, _VP],
     "mtgp_plan_autotune": [_VP, ctypes.POINTER(LaunchConfig)],
     "mtgp_plan_get_info": [_VP, ctypes.POINTER(PlanInfo)],
     "mtgp_plan_set_trace": [_VP, ctypes.c_int],
@@ -267,10 +275,12 @@ class Streams:
 class Plan:
     """Owning wrapper of an mtgp_plan_t (keeps its Streams alive)."""
 
-    def __init__(self, handle, streams, out):
+    def __init__(self, handle, streams, out, n_req=0):
         self.handle = handle
         self.streams = streams
         self.out = out
+        self.n_req = n_req
+        self.stats = None   # (gap t or 0, weight classes C or 0) while statistics are on
 
     def close(self):
         if self.handle:
@@ -429,7 +439,7 @@ def mtgp_plan_create(streams: Streams, stream_ids, counts, fmt, out) -> Plan:
     h = _VP()
     _call("mtgp_plan_create", streams.handle, _p32(ids), _p64(counts), ids.size, int(fmt),
           _dev_ptr(out, total), ctypes.byref(h))
-    return Plan(h, streams, out)
+    return Plan(h, streams, out, ids.size)
 
 
 def mtgp_plan_launch(plan: Plan, stream=None):
@@ -438,6 +448,42 @@ def mtgp_plan_launch(plan: Plan, stream=None):
 
 def mtgp_plan_set_split(plan: Plan, max_piece: int):
     _call("mtgp_plan_set_split", plan.handle, int(max_piece))
+
+
+def mtgp_plan_set_stats(plan: Plan, gap=None, hamming=None):
+    """Fuse the statistics of tests 35 and 100 (Sec. 4.2) into the plan's
+    launches, per request: gap = (r, b, t) or None, hamming = (r, s, L,
+    bounds) or None; both None turns them off."""
+    if gap is None and hamming is None:
+        _call("mtgp_plan_set_stats", plan.handle, None)
+        plan.stats = None
+        return
+    c = StatsConfig()
+    if gap is not None:
+        c.gap_r, c.gap_b, c.gap_t = (int(v) for v in gap)
+    if hamming is not None:
+        r, s, L, bounds = hamming
+        bnd = [int(b) for b in bounds]
+        if len(bnd) > 15:
+            raise ValueError("at most 15 bounds")
+        c.ham_r, c.ham_s, c.ham_L, c.n_bounds = int(r), int(s), int(L), len(bnd)
+        for i, b in enumerate(bnd):
+            c.bounds[i] = b
+    _call("mtgp_plan_set_stats", plan.handle, ctypes.byref(c))
+    plan.stats = (c.gap_t, (c.n_bounds + 1) if c.ham_L else 0)
+
+
+def mtgp_plan_read_stats(plan: Plan, stream=None):
+    """Counts of the plan's last launch: (hist (n_req, t+1) or None,
+    table (n_req, C, C) or None)."""
+    if plan.stats is None:
+        raise MtgpError(1, "the plan computes no statistics")
+    t, C = plan.stats
+    hist = np.zeros((plan.n_req, t + 1), np.uint64) if t else None
+    tab = np.zeros((plan.n_req, C, C), np.uint64) if C else None
+    _call("mtgp_plan_read_stats", plan.handle, _p64(hist) if hist is not None else None,
+          _p64(tab) if tab is not None else None, _stream_handle(stream))
+    return hist, tab
 
 
 def mtgp_plan_autotune(plan: Plan) -> dict:
@@ -465,7 +511,8 @@ def mtgp_plan_get_info(plan: Plan) -> dict:
             "kernel_launches": i.kernel_launches, "config": i.config.as_dict(),
             "grid_ctas": i.grid_ctas, "n_coop": i.n_coop, "regs_per_thread": i.regs_per_thread,
             "resident_ctas_per_sm": i.resident_ctas_per_sm, "max_piece": i.max_piece,
-            "n_split_streams": i.n_split_streams, "n_jumps": i.n_jumps, "n_pieces": i.n_pieces}
+            "n_split_streams": i.n_split_streams, "n_jumps": i.n_jumps, "n_pieces": i.n_pieces,
+            "stats": bool(i.stats)}
 
 
 class Server:
