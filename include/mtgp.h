@@ -323,7 +323,7 @@ typedef struct {
  * memory; mtgp_plan_read_stats returns them.  cfg = NULL (or both tests
  * left out) returns the plan to the plain generation kernel.
  * MTGP_EINVAL: parameters out of range; a split plan or one with tracing
- * on; a request of 2^32 numbers or more; a parameter set with N - pos < 256
+ * on; a request of 2^31 numbers or more; a parameter set with N - pos < 256
  * or a state size without an instantiation of the fused kernel (the
  * exponents whose ceil(N/32) is 10, 11, 20, 22, 23 or 44, e.g. 11213, 23209
  * and 44497).  Re-records the plan's graph; synchronous.  No counterpart in

@@ -474,7 +474,7 @@ static mtgp_status init_handle(const mtgp_mt_params* sets, uint32_t n_sets, cons
         const void* fn = mt_kernel_ptr(h->K);
         h->threads = 32 * kWarpsPerCta;
         h->smem = (size_t)kWarpsPerCta * k.stride * 4u;
-        if (h->smem > 48u * 1024u && (e = allow_max_dynamic_smem(fn, h->device, h->smem)) != cudaSuccess)
+        if ((e = allow_max_dynamic_smem(fn, h->device, h->smem)) != cudaSuccess)
             return bail(e, "dynamic shared memory limit");
         int per_sm = 0, sms = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, h->threads, h->smem)) !=

@@ -5,118 +5,160 @@
 //
 // The generator is mtgp_fast_kernel's single-warp, software-pipelined row
 // loop (128-word steps, N - pos >= 256; see mtgp_fast.cuh), unchanged except
-// that every sub-step's 32 outputs (31 in a row's last sub-step when
-// N = 351) also pass through stats_run.  A sequence of the statistics is one
-// request of the launch (Segment::req): its values in generation order.
+// that the outputs of every sub-step also feed the statistics.  A sequence
+// of the statistics is one request of the launch (Segment::req): its values
+// in generation order.  Each request belongs to one warp, which writes its
+// histogram and table rows when the request ends.
 //
-// Per sub-step, for a run of consecutive lanes [l0, l0 + n) of one sequence:
-//   gap test -- a value visits when (value & gmask) == 0; the visits form a
-//     ballot B; a visiting lane's gap is the number of non-visits since the
-//     previous visit: its distance to the nearest lower visiting lane, or,
-//     when none, lane - l0 plus the carried run D of non-visits before the
-//     run (counted from the sequence's start, so the first visit's gap is
-//     counted too).  Lengths >= t are pooled in class t; a trailing run of
-//     non-visits is not a gap.
-//   Hamming -- the weight popc(value & hmask) of each value adds to the
-//     first or second block of the current pair (K values per block) by the
-//     value's position in the pair; per-lane partial sums are reduced when a
-//     pair completes, and lane 0 counts (class of first, class of second)
-//     in the warp's table.  An incomplete trailing pair is ignored.
-// Each sequence belongs to one warp, which writes its histogram and table
-// rows when the sequence ends.  Ballots, shuffles and reductions run in
-// warp-uniform control flow; lane-dependent branches hold only shared-memory
-// updates.
+// Gap test, per sub-step, over a run of lanes [l0, l0 + n) of one request:
+// a value visits when (value & gmask) == 0; the visits form a ballot B.  A
+// visiting lane's gap (non-visits since the previous visit) is its distance
+// to the nearest lower visiting lane, or, when there is none, lane - l0 plus
+// the carried count D of non-visits since the request's last visit (or its
+// start: the first visit's gap counts too).  Lengths >= t are pooled in
+// class t; a trailing run of non-visits is not a gap.  Each sub-step ends in
+// one shared-memory reduction per lane (red.shared.add, no return): a
+// visiting lane adds 1 to its class in the warp's histogram, the others to
+// a slot of their own that is never read, so the reduction needs neither a
+// predicate nor a branch.  In full rows the step's reductions are issued
+// after the step's row stores and warp barrier, so that they do not delay
+// them.
+//
+// Hamming test: the weights popc(value & hmask) of K = L/s consecutive
+// values form a block; `rem` counts the values left in the current block,
+// and each lane keeps its part of the block's weight.  A step that contains
+// no block end (rem > values of the step) only adds the weights; a step that
+// contains one splits its lanes at the end, reduces the finished block's
+// weight across the warp and, on every second block, counts the pair
+// (class of first, class of second) in the warp's shared-memory table.  The
+// class of a weight is the number of bounds <= it: lane i holds bound i, and
+// a ballot counts them.  An incomplete trailing pair is
+// ignored.  K >= 128 keeps every 128-value step to at most one block end;
+// smaller K take the per-sub-step form (K >= 32: at most one block end per
+// sub-step).
+//
+// Ballots, shuffles and reductions run in warp-uniform control flow.
 #pragma once
 
 #include "mtgp_fast.cuh"
 
 namespace mtgp {
 
-// The warp's running statistics of its current sequence.
+// The warp's running statistics of its current request (all fields but acc
+// and bnd are uniform across the warp).
 struct StatsState {
-    uint32_t seq;    // current sequence (request index), kNoSeq = none
-    uint32_t D;      // non-visits since the last visit (saturating)
-    uint32_t pos;    // position of the next value within the current block pair
-    uint32_t acc_a;  // this lane's partial weight of the pair's first block
-    uint32_t acc_b;  // ... and of its second block
+    uint32_t seq;    // current request (index in the launch), kNoSeq = none
+    uint32_t D;      // gap test: non-visits since the last visit (< 2^31)
+    uint32_t rem;    // Hamming: values left in the current block, 1 .. K
+    uint32_t half;   // Hamming: 1 when the current block is its pair's second
+    uint32_t wa;     // Hamming: weight of the pair's first block (half = 1)
+    uint32_t acc;    // this lane's part of the current block's weight
+    uint32_t bnd;    // this lane's class bound (lanes 0 .. C-2), else ~0
 };
 constexpr uint32_t kNoSeq = 0xFFFFFFFFu;
-constexpr uint32_t kMaxRun = 0x3FFFFFFFu;
 
-__device__ __forceinline__ void stats_run(uint32_t o, uint32_t l0, uint32_t n, uint32_t lane,
-                                          StatsState& st, uint32_t* h, uint32_t* tab,
-                                          const StatsArgs& A)
+// Position of the highest set bit, 0xFFFFFFFF for 0 (PTX bfind).
+__device__ __forceinline__ uint32_t hibit(uint32_t x)
 {
-    const bool lane_in = lane >= l0 && lane < l0 + n;
-    if (A.gmask) {
-        const bool in = lane_in && (o & A.gmask) == 0u;
-        const uint32_t B = __ballot_sync(MTGP_FULL, in);
-        const uint32_t below = B & ((1u << lane) - 1u);
-        const uint32_t gap = below ? lane - 1u - (31u - (uint32_t)__clz(below)) : lane - l0 + st.D;
-        if (in)
-            atomicAdd(&h[min(gap, A.t)], 1u);
-        st.D = B ? l0 + n - 1u - (31u - (uint32_t)__clz(B)) : min(st.D + n, kMaxRun);
+    uint32_t r;
+    asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x));
+    return r;
+}
+
+// Adds 1 to the shared-memory word at 32-bit shared address a.
+__device__ __forceinline__ void count_at(uint32_t a)
+{
+    asm volatile("red.shared.add.u32 [%0], 1;" :: "r"(a));
+}
+
+// Gap test over lanes [l0, l0 + n) of one request; `valid` = lane in them.
+// Returns the shared address this lane counts at: its class in the
+// histogram hs when it visits, else its own slot `own`.
+__device__ __forceinline__ uint32_t gap_run(uint32_t o, bool valid, uint32_t l0, uint32_t n, uint32_t lane,
+                                            uint32_t lower, StatsState& st, uint32_t hs, uint32_t own,
+                                            const StatsArgs& A)
+{
+    const bool in = valid && (o & A.gmask) == 0u;
+    const uint32_t B = __ballot_sync(MTGP_FULL, in);
+    const uint32_t hb = hibit(B & lower);   // nearest lower visiting lane, or ~0
+    const uint32_t gap = hb != 0xFFFFFFFFu ? lane - hb - 1u : lane - l0 + st.D;
+    st.D = B ? l0 + n - 1u - hibit(B) : st.D + n;
+    return in ? hs + 4u * min(gap, A.t) : own;
+}
+
+// A Hamming block of weight W has ended: the first of a pair is kept, the
+// second completes the pair, which lane 0 counts in the warp's table.
+__device__ __forceinline__ void block_done(uint32_t W, uint32_t lane, StatsState& st, uint32_t* tab,
+                                           const StatsArgs& A)
+{
+    if (st.half) {
+        const uint32_t ca = __popc(__ballot_sync(MTGP_FULL, st.bnd <= st.wa));
+        const uint32_t cb = __popc(__ballot_sync(MTGP_FULL, st.bnd <= W));
+        if (lane == 0u)
+            tab[ca * A.C + cb] += 1u;
     }
-    if (A.hmask) {
-        const uint32_t w = __popc(o & A.hmask);
-        const uint32_t p = st.pos + lane - l0;   // meaningful for lanes in the run
-        if (lane_in && p < A.K)
-            st.acc_a += w;
-        else if (lane_in && p < 2u * A.K)
-            st.acc_b += w;
-        if (st.pos + n >= 2u * A.K) {   // the pair completes in this run (2K > 32)
-            const uint32_t wa = __reduce_add_sync(MTGP_FULL, st.acc_a);
-            const uint32_t wb = __reduce_add_sync(MTGP_FULL, st.acc_b);
-            if (lane == 0u) {
-                uint32_t ca = 0u, cb = 0u;
-#pragma unroll
-                for (uint32_t i = 0; i < 15u; ++i) {
-                    if (i + 1u < A.C) {
-                        ca += A.bounds[i] <= wa;
-                        cb += A.bounds[i] <= wb;
-                    }
-                }
-                tab[ca * A.C + cb] += 1u;
-            }
-            st.acc_a = (lane_in && p >= 2u * A.K) ? w : 0u;
-            st.acc_b = 0u;
-            st.pos = st.pos + n - 2u * A.K;
-        } else {
-            st.pos += n;
-        }
+    st.wa = W;
+    st.half ^= 1u;
+}
+
+// Hamming test over lanes [l0, l0 + n) of one request (n <= 32 <= K: at
+// most one block end); w = this lane's weight (0 outside the run).
+__device__ __forceinline__ void ham_run(uint32_t w, uint32_t l0, uint32_t n, uint32_t lane,
+                                        StatsState& st, uint32_t* tab, const StatsArgs& A)
+{
+    if (st.rem > n) {
+        st.acc += w;
+        st.rem -= n;
+    } else {
+        const bool next = lane >= l0 + st.rem;   // after the block's end
+        const uint32_t W = __reduce_add_sync(MTGP_FULL, st.acc + (next ? 0u : w));
+        st.acc = next ? w : 0u;
+        block_done(W, lane, st, tab, A);
+        st.rem = st.rem + A.K - n;
     }
 }
 
-// Writes the current sequence's histogram and table rows and starts `next`.
+// Writes the current request's histogram and table rows (where the launch
+// asks for them) and starts request `next`.
 __device__ __forceinline__ void stats_switch(StatsState& st, uint32_t next, uint32_t lane, uint32_t* h,
                                              uint32_t* tab, const StatsArgs& A)
 {
     if (st.seq == next)
         return;
-    __syncwarp();
     if (st.seq != kNoSeq) {
-        if (A.gmask)
-            for (uint32_t i = lane; i <= A.t; i += 32u) {
+        __syncwarp();
+        for (uint32_t i = lane; i <= A.t; i += 32u) {
+            if (A.hist)
                 A.hist[(size_t)st.seq * (A.t + 1u) + i] = h[i];
-                h[i] = 0u;
-            }
-        if (A.hmask)
-            for (uint32_t i = lane; i < A.C * A.C; i += 32u) {
+            h[i] = 0u;
+        }
+        for (uint32_t i = lane; i < A.C * A.C; i += 32u) {
+            if (A.tab)
                 A.tab[(size_t)st.seq * A.C * A.C + i] = tab[i];
-                tab[i] = 0u;
-            }
+            tab[i] = 0u;
+        }
+        __syncwarp();
     }
-    __syncwarp();
     st.seq = next;
     st.D = 0u;
-    st.pos = 0u;
-    st.acc_a = 0u;
-    st.acc_b = 0u;
+    st.rem = A.K;
+    st.half = 0u;
+    st.wa = 0u;
+    st.acc = 0u;
+}
+
+// Shared addresses of the warp's histogram and of this lane's own slot
+// (the 32 words after the histogram).
+__device__ __forceinline__ uint32_t hist_addr(const uint32_t* h) { return (uint32_t)__cvta_generic_to_shared(h); }
+__device__ __forceinline__ uint32_t own_addr(const uint32_t* h, uint32_t lane, const StatsArgs& A)
+{
+    return (uint32_t)__cvta_generic_to_shared(h + ((A.t + 1u + 3u) & ~3u) + lane);
 }
 
 // nfull consecutive full rows of one request (as gen_rows_pipelined, K = 4),
-// with the statistics of every sub-step's outputs.
-template <int M, int FMT>
+// with the statistics of every sub-step's outputs.  STEPH: Hamming per step
+// (K >= 128), else per sub-step.
+template <int M, int FMT, bool STEPH>
 __device__ __forceinline__ void fused_rows(uint32_t (&r)[M], uint32_t* Sw, uint32_t* ow, const uint32_t* Q,
                                            const RowP& P, uint32_t lane, const uint32_t* __restrict__ Tb,
                                            uint32_t last_lane, uint32_t nfull, StatsState& st, uint32_t* h,
@@ -125,6 +167,11 @@ __device__ __forceinline__ void fused_rows(uint32_t (&r)[M], uint32_t* Sw, uint3
     constexpr int K = 4;
     constexpr int NS = (M + K - 1) / K;
     const uint32_t N = P.n;
+    const uint32_t lower = (1u << lane) - 1u;
+    const bool last_ok = lane <= last_lane;     // lane holds a column of the row's last group
+    const uint32_t nlast = last_lane + 1u;      // columns of the last group
+    const uint32_t hs = hist_addr(h);
+    const uint32_t own = own_addr(h, lane, A);
     uint32_t x1[K], xp[K], xq[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
@@ -146,7 +193,7 @@ __device__ __forceinline__ void fused_rows(uint32_t (&r)[M], uint32_t* Sw, uint3
                     yq[i] = Q[32 * (n0 + i) - 1];
                 }
             }
-            uint32_t xn[K], o[K];
+            uint32_t xn[K], o[K], w[K], ad[K];
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 if (s0 + i < M) {
@@ -156,14 +203,48 @@ __device__ __forceinline__ void fused_rows(uint32_t (&r)[M], uint32_t* Sw, uint3
                     o[i] = temper_convert<FMT>(xn[i], temper_index(xq[i]), Tb);
                 }
             }
+            // statistics of this step's outputs
 #pragma unroll
-            for (int i = 0; i < K; ++i)
-                if (s0 + i < M)
-                    stats_run(o[i], 0u, s0 + i + 1 < M ? 32u : last_lane + 1u, lane, st, h, tab, A);
+            for (int i = 0; i < K; ++i) {
+                if (s0 + i < M) {
+                    const bool lastg = s0 + i + 1 == M;
+                    const bool valid = !lastg || last_ok;
+                    ad[i] = gap_run(o[i], valid, 0u, lastg ? nlast : 32u, lane, lower, st, hs, own, A);
+                    w[i] = valid ? __popc(o[i] & A.hmask) : 0u;
+                    if constexpr (!STEPH)
+                        ham_run(w[i], 0u, lastg ? nlast : 32u, lane, st, tab, A);
+                }
+            }
+            if constexpr (STEPH) {
+                const int KS = (M - s0 < K) ? M - s0 : K;   // sub-steps in this step
+                const uint32_t step_n = (s0 + KS == M) ? 32u * (KS - 1) + nlast : 32u * KS;
+                if (st.rem > step_n) {
+                    uint32_t a = st.acc;
+#pragma unroll
+                    for (int i = 0; i < KS; ++i)
+                        a += w[i];
+                    st.acc = a;
+                    st.rem -= step_n;
+                } else {
+                    // the block ends inside this step: step positions >= rem
+                    // belong to the next block
+                    uint32_t cur = st.acc, nxt = 0u;
+#pragma unroll
+                    for (int i = 0; i < KS; ++i) {
+                        const bool after = 32u * (uint32_t)i + lane >= st.rem;
+                        cur += after ? 0u : w[i];
+                        nxt += after ? w[i] : 0u;
+                    }
+                    const uint32_t W = __reduce_add_sync(MTGP_FULL, cur);
+                    st.acc = nxt;
+                    block_done(W, lane, st, tab, A);
+                    st.rem = st.rem + A.K - step_n;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const int m = s0 + i;
-                if (m < M && (m + 1 < M || lane <= last_lane)) {
+                if (m < M && (m + 1 < M || last_ok)) {
                     r[m] = xn[i];
                     Sw[32 * m] = xn[i];
                     if (32u * (uint32_t)m < P.mirror)
@@ -174,6 +255,8 @@ __device__ __forceinline__ void fused_rows(uint32_t (&r)[M], uint32_t* Sw, uint3
             __syncwarp();
 #pragma unroll
             for (int i = 0; i < K; ++i) {
+                if (s0 + i < M)
+                    count_at(ad[i]);
                 if (n0 + i < M) {
                     x1[i] = y1[i];
                     xp[i] = yp[i];
@@ -195,6 +278,7 @@ __device__ __forceinline__ void fused_row_slow(uint32_t (&r)[M], uint32_t* Sw, c
                                                uint32_t s_first, uint32_t s_end, uint32_t* __restrict__ out,
                                                StatsState& st, uint32_t* h, uint32_t* tab, const StatsArgs& A)
 {
+    const uint32_t lower = (1u << lane) - 1u;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         if (32u * (uint32_t)m >= n_valid)
@@ -229,8 +313,11 @@ __device__ __forceinline__ void fused_row_slow(uint32_t (&r)[M], uint32_t* Sw, c
             const uint32_t l0 = (uint32_t)__ffs(remaining) - 1u;
             const uint32_t r0 = __shfl_sync(MTGP_FULL, req, l0);
             const uint32_t same = __ballot_sync(MTGP_FULL, valid && req == r0) & remaining;
+            const uint32_t n = (uint32_t)__popc(same);
+            const bool in_run = (same >> lane) & 1u;
             stats_switch(st, r0, lane, h, tab, A);
-            stats_run(o, l0, (uint32_t)__popc(same), lane, st, h, tab, A);
+            count_at(gap_run(o, in_run, l0, n, lane, lower, st, hist_addr(h), own_addr(h, lane, A), A));
+            ham_run(in_run ? __popc(o & A.hmask) : 0u, l0, n, lane, st, tab, A);
             remaining &= ~same;
         }
         __syncwarp();
@@ -288,12 +375,21 @@ __device__ __forceinline__ void fused_item(const KParams& KP, const RowP& P, uin
             const uint32_t nfull = (uint32_t)min((seg_end - row) / N, (uint64_t)0xFFFFFFFFu);
             uint32_t* ow = out + sg.out_off + (row - sg.g_start) + lane;
             stats_switch(st, sg.req, lane, h, tab, A);
-            if (sg.fmt == 0)
-                fused_rows<M, 0>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
-            else if (sg.fmt == 1)
-                fused_rows<M, 1>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
-            else
-                fused_rows<M, 2>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+            if (A.K >= 128u) {
+                if (sg.fmt == 0)
+                    fused_rows<M, 0, true>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+                else if (sg.fmt == 1)
+                    fused_rows<M, 1, true>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+                else
+                    fused_rows<M, 2, true>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+            } else {
+                if (sg.fmt == 0)
+                    fused_rows<M, 0, false>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+                else if (sg.fmt == 1)
+                    fused_rows<M, 1, false>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+                else
+                    fused_rows<M, 2, false>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+            }
             row += (uint64_t)nfull * N;
         } else {
             const uint64_t left = total - row;
@@ -336,12 +432,16 @@ __global__ void __launch_bounds__(G * 32) mtgp_fused_kernel(const KParams P, uin
     const uint32_t row_words = fast_smem_words(P.n, P.mirror);
     uint32_t* S = smem + warp * (row_words + stats_smem_words(A.t, A.C));
     uint32_t* h = S + row_words;
-    uint32_t* tab = h + ((A.t + 1u + 3u) & ~3u);
+    uint32_t* tab = h + ((A.t + 1u + 3u) & ~3u) + 32u;
     for (uint32_t i = lane; i < stats_smem_words(A.t, A.C); i += 32u)
         h[i] = 0u;
     __syncthreads();
     const RowP R0 = {P.n, P.mask, P.pos, P.sh1, P.sh2, P.mirror};
-    StatsState st = {kNoSeq, 0u, 0u, 0u, 0u};
+    StatsState st = {kNoSeq, 0u, A.K, 0u, 0u, 0u, 0xFFFFFFFFu};
+#pragma unroll
+    for (uint32_t i = 0; i < 15u; ++i)
+        if (lane == i && i + 1u < A.C)
+            st.bnd = A.bounds[i];
     for (;;) {
         uint32_t it = 0;
         if (lane == 0)

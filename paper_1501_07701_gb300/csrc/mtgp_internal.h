@@ -83,11 +83,13 @@ __host__ __device__ inline uint32_t ring_smem_words(uint32_t n) { return 32u + (
 // shifts are in 1..31.
 bool fast_supported(const KParams& P, int k, int g = 4);
 
-// Lets `fn` launch with up to the device's opt-in maximum of dynamic shared
-// memory (cudaErrorInvalidValue if `need` exceeds it).  The limit is a
-// process-wide attribute of the function, so it is always raised to that
-// maximum: a per-handle value could lower it under another live handle.
-// Occupancy still follows each launch's own size.
+// Lets `fn` launch with `need` bytes of dynamic shared memory: when need plus
+// the function's static shared memory exceeds the 48 KB available without
+// opt-in, the function's dynamic limit is raised to the device's opt-in
+// maximum less its static shared memory (cudaErrorInvalidValue if `need`
+// exceeds that).  The limit is a process-wide attribute of the function, so
+// it is always raised to that maximum: a per-handle value could lower it
+// under another live handle.  Occupancy still follows each launch's own size.
 cudaError_t allow_max_dynamic_smem(const void* fn, int device, size_t need);
 
 // Seed status -> state rows (row stride P.np words; padding words zeroed).
@@ -170,11 +172,13 @@ struct StatsArgs {
     unsigned long long* tab;       // n_req x C x C counts
 };
 
-// Shared-memory words per warp that the statistics add: the histogram and
-// the table of the warp's current request, each rounded up to 4 words.
+// Shared-memory words per warp that the statistics add: the gap histogram
+// of the warp's current request (rounded up to 4 words), one slot per lane
+// that absorbs the counts of non-visiting lanes, and the request's C x C
+// pair table (rounded up to 4 words).
 __host__ __device__ inline uint32_t stats_smem_words(uint32_t t, uint32_t C)
 {
-    return ((t + 1u + 3u) & ~3u) + ((C * C + 3u) & ~3u);
+    return ((t + 1u + 3u) & ~3u) + 32u + ((C * C + 3u) & ~3u);
 }
 
 // The fused generation kernel (single-warp items, 128-word pipelined steps,

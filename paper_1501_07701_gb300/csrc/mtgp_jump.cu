@@ -838,19 +838,16 @@ mtgp_status mtgp::build_jump_batch(mtgp_streams* st, const std::vector<uint32_t>
     // a zero g (possible only if t^(J-1) = 0 mod mu, which needs t | mu):
     // the kernel then accumulates nothing and applies one step to 0
     out->smem = ((size_t)max_deg + 1 + N - 1 + N) * 4;
-    int dev = 0, max_smem = 0;
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess)
-        return fail_cuda(e, "device attributes");
-    if (out->smem + 64 > (size_t)max_smem)
+        return fail_cuda(e, "cudaGetDevice");
+    e = allow_max_dynamic_smem((const void*)mtgp_jump_kernel, dev, out->smem);
+    if (e == cudaErrorInvalidValue)
         return fail(MTGP_EINVAL, "state size too large for the jump kernel (%zu bytes of shared memory)",
                     out->smem);
-    e = cudaFuncSetAttribute((const void*)mtgp_jump_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)out->smem);
     if (e != cudaSuccess)
-        return fail_cuda(e, "cudaFuncSetAttribute(jump kernel)");
+        return fail_cuda(e, "jump kernel shared memory limit");
     return MTGP_OK;
 }
 

@@ -207,13 +207,23 @@ cudaError_t launch_copy_rows(const uint32_t* src, uint32_t* dst, const uint2* pa
 // ---------------------------------------------------------------------------
 cudaError_t allow_max_dynamic_smem(const void* fn, int device, size_t need)
 {
-    int optin = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    // Without the opt-in a CTA may use 48 KB of static and dynamic shared
+    // memory together; beyond that the function's dynamic limit is raised
+    // to the device's opt-in maximum less its static shared memory.
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess)
         return e;
-    if (need > (size_t)optin)
+    if (need + fa.sharedSizeBytes <= 48u * 1024u)
+        return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess)
+        return e;
+    if (need + fa.sharedSizeBytes > (size_t)optin)
         return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
 }
 
 static int fast_m(const KParams& P) { return (int)((P.n + 31u) / 32u); }
@@ -265,7 +275,7 @@ cudaError_t plan_geometry(const KParams& P, const LaunchCfg& cfg, uint32_t n_ite
         fn = (const void*)mtgp_ring_kernel;
     }
     cudaError_t e;
-    if (g->smem > 48u * 1024u && (e = allow_max_dynamic_smem(fn, device, g->smem)) != cudaSuccess)
+    if ((e = allow_max_dynamic_smem(fn, device, g->smem)) != cudaSuccess)
         return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g->threads, g->smem);

@@ -181,6 +181,32 @@ def test_other_exponents(mexp):
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("k", [4, 8])
+@pytest.mark.parametrize("mexp", [23209, 44497])
+def test_eight_warp_ctas_of_large_states(mexp, k, kernel):
+    """8-warp CTAs of the largest state sizes need about 48 KB of shared
+    memory or more, static and dynamic together: the launch must take the
+    configuration as given (no fallback) and equal the oracle."""
+    gp, op = _both_params(mexp)
+    n = 24
+    st = mtgp.mtgp_init_statuses(gp, np.arange(n, dtype=np.uint32))
+    mtgp.mtgp_set_launch_config(st, warps_per_cta=8, words_per_lane=k, kernel=kernel, ctas_per_sm=0)
+    states = mtgp.mtgp_get_statuses(st)
+    ids = np.arange(n, dtype=np.uint32)
+    counts = np.array([(i * 104729) % 300000 + 1 for i in range(n)], np.uint64)
+    out = torch.empty(int(counts.sum()), dtype=torch.int32, device="cuda")
+    plan = mtgp.mtgp_plan_create(st, ids, counts, mtgp.MTGP_U32, out)
+    info = mtgp.mtgp_plan_get_info(plan)
+    assert info["config"]["warps_per_cta"] == 8 and info["config"]["kernel"] == kernel
+    mtgp.mtgp_plan_launch(plan)
+    torch.cuda.synchronize()
+    mtgp.mtgp_check(st)
+    ref, states = oracle.generate_many(op, states, ids, counts, 0, THREADS)
+    _assert_same(out.cpu().numpy().view(np.uint32), ref, "mexp %d k %d kernel %d" % (mexp, k, kernel))
+    _assert_same(mtgp.mtgp_get_statuses(st), states)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("mexp", [9689, 11213, 19937, 21701, 23209, 44497])
 @pytest.mark.parametrize("pseed", [1, 2, 3])
 def test_parameter_sweep(kernel, mexp, pseed):
