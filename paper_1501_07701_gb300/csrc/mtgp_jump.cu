@@ -410,9 +410,9 @@ __global__ void __launch_bounds__(256) mtgp_jump_kernel(const KParams P, uint32_
         acc[j] = 0u;
     }
     __syncthreads();
-    // expand: S[i + N] for i = 0 .. D-2, Wc words per step (each reads only
-    // words produced before the step: Wc <= N - pos)
-    const uint32_t Wc = min(32u, N - pos);
+    // expand: S[i + N] for i = 0 .. D-2, Wc words per step, one per thread
+    // (each reads only words produced before the step: Wc <= N - pos)
+    const uint32_t Wc = min(blockDim.x, N - pos);
     for (uint32_t i0 = 0; i0 + 1u < D; i0 += Wc) {
         const uint32_t i = i0 + threadIdx.x;
         uint32_t v = 0;
@@ -428,28 +428,39 @@ __global__ void __launch_bounds__(256) mtgp_jump_kernel(const KParams P, uint32_
             S[i + N] = v;
         __syncthreads();
     }
-    // accumulate: warp w takes the set bits k of g with k / 32 = w (mod warps)
+    // accumulate: warp w takes the set bits k of g with k / 32 = w (mod
+    // warps); acc[j] ^= S[k + j] for every such k.  The N words are covered
+    // in nch passes of uc <= 12 units of 32 words (one word per lane per
+    // unit), so that a pass wastes at most one unit's loads.
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t* gp = polys + (size_t)it.poly * poly_words;
-    for (uint32_t j0 = 0; j0 < N; j0 += 32u * 8u) {
-        uint32_t a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    constexpr uint32_t kUnits = 12;
+    const uint32_t U = (N + 31u) / 32u;
+    const uint32_t nch = (U + kUnits - 1u) / kUnits;
+    const uint32_t uc = (U + nch - 1u) / nch;
+    for (uint32_t c = 0; c < nch; ++c) {
+        const uint32_t j0 = 32u * uc * c;
+        uint32_t a[kUnits];
+#pragma unroll
+        for (uint32_t q = 0; q < kUnits; ++q)
+            a[q] = 0u;
         for (uint32_t w = warp; w * 32u < D; w += nw) {
             uint32_t bits = gp[w];
             while (bits) {
                 const uint32_t k = w * 32u + (uint32_t)(__ffs(bits) - 1);
                 bits &= bits - 1u;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (uint32_t q = 0; q < kUnits; ++q) {
                     const uint32_t j = j0 + 32u * q + lane;
-                    if (j < N)
+                    if (q < uc && j < N)
                         a[q] ^= S[k + j];
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (uint32_t q = 0; q < kUnits; ++q) {
             const uint32_t j = j0 + 32u * q + lane;
-            if (j < N && a[q])
+            if (q < uc && j < N && a[q])
                 atomicXor(&acc[j], a[q]);
         }
     }
