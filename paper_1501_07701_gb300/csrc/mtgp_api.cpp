@@ -536,6 +536,8 @@ static void destroy_streams(mtgp_streams* h)
     }
     if (h->copy_stream)
         cudaStreamDestroy(h->copy_stream);
+    if (h->d_chunk_tables)
+        cudaFree(h->d_chunk_tables);
     if (h->d_states)
         cudaFree(h->d_states);
     if (h->d_err)
@@ -805,6 +807,21 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
     fill_table(w, sl.host);
     CUDA_TRY(cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, s),
              "cudaMemcpyAsync(work table)");
+    mtgp_status stt = launch_work_table(st, w, sl.dev, cfg, out, s);
+    if (stt != MTGP_OK)
+        return stt;
+    CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
+    sl.ev_recorded = true;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp::launch_work_table(mtgp_streams* st, const Work& w, void* table, const LaunchCfg& cfg,
+                                    void* out, cudaStream_t s)
+{
+    if (w.items.empty())
+        return MTGP_OK;
+    size_t io, so;
+    table_bytes(w, &io, &so);
     Geometry g;
     mtgp_status stt = geometry_for(st, cfg, (uint32_t)w.items.size(), &g);
     if (stt != MTGP_OK)
@@ -813,19 +830,17 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
     a.P = st->P.k;
     a.states = st->d_states;
     a.n_streams = st->n_streams;
-    a.items = (const WorkItem*)((char*)sl.dev + io);
-    a.segs = (const Segment*)((char*)sl.dev + so);
+    a.items = (const WorkItem*)((char*)table + io);
+    a.segs = (const Segment*)((char*)table + so);
     a.n_items = (uint32_t)w.items.size();
     a.n_coop = st->d_sets ? 0u : coop_count(w, g, cfg.coop_percent);
-    a.counter = (uint32_t*)sl.dev;
+    a.counter = (uint32_t*)table;
     a.out = (uint32_t*)out;
     a.err = st->d_err;
     a.trace = nullptr;
     a.sets = st->d_sets;
     a.set_of = st->d_set_of;
     CUDA_TRY(launch_generate(a, g, s), "generation kernel launch");
-    CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
-    sl.ev_recorded = true;
     return MTGP_OK;
 }
 
@@ -903,59 +918,88 @@ extern "C" mtgp_status mtgp_generate_to_host(mtgp_streams_t st, const uint32_t* 
     }
     // Split the request list into chunks of at most `chunk` numbers; a long
     // request becomes consecutive requests of the same stream, which draw
-    // the same numbers.
-    std::vector<uint32_t> cid;
-    std::vector<uint64_t> ccount;
-    uint64_t host_off = 0;
-    uint64_t fill = 0;
-    int nchunk = 0;
-    bool recorded[mtgp_streams::kStages] = {};
-    auto flush = [&]() -> mtgp_status {
-        if (fill == 0)
+    // the same numbers.  Every chunk's work table is built first and all of
+    // them are uploaded in one copy, so that no host-to-device transfer sits
+    // between a chunk's generation and the previous chunk's copy to the host.
+    std::vector<Work> works;
+    std::vector<uint64_t> fills;
+    {
+        std::vector<uint32_t> cid;
+        std::vector<uint64_t> ccount;
+        uint64_t fill = 0;
+        auto close = [&]() -> mtgp_status {
+            if (fill == 0)
+                return MTGP_OK;
+            works.emplace_back();
+            mtgp_status s = build_work(st->n_streams, cid.data(), ccount.data(), nullptr, fmt,
+                                       (uint32_t)cid.size(), 0, works.back());
+            if (s != MTGP_OK)
+                return s;
+            fills.push_back(fill);
+            fill = 0;
+            cid.clear();
+            ccount.clear();
             return MTGP_OK;
-        const int b = nchunk % mtgp_streams::kStages;
-        if (recorded[b])
-            CUDA_TRY(cudaStreamWaitEvent(cs, st->ev_copy[b], 0), "cudaStreamWaitEvent");
-        Work w;
-        mtgp_status s = build_work(st->n_streams, cid.data(), ccount.data(), nullptr, fmt,
-                                   (uint32_t)cid.size(), 0, w);
+        };
+        for (uint32_t j = 0; j < n_req; ++j) {
+            uint64_t left = counts[j];
+            while (left) {
+                const uint64_t take = std::min(left, chunk - fill);
+                cid.push_back(ids[j]);
+                ccount.push_back(take);
+                fill += take;
+                left -= take;
+                if (fill == chunk) {
+                    mtgp_status s = close();
+                    if (s != MTGP_OK)
+                        return s;
+                }
+            }
+        }
+        mtgp_status s = close();
         if (s != MTGP_OK)
             return s;
-        s = launch_work(st, w, st->cfg, st->stage[b], cs);
+    }
+    std::vector<size_t> toff(works.size());
+    size_t tbytes = 0;
+    for (size_t c = 0; c < works.size(); ++c) {
+        toff[c] = tbytes;
+        tbytes += (table_bytes(works[c], nullptr, nullptr) + 255u) & ~(size_t)255u;
+    }
+    std::vector<char> tables(tbytes);
+    for (size_t c = 0; c < works.size(); ++c)
+        fill_table(works[c], tables.data() + toff[c]);
+    if (tbytes > st->chunk_tables_cap) {
+        if (st->d_chunk_tables)
+            cudaFree(st->d_chunk_tables);
+        st->d_chunk_tables = nullptr;
+        st->chunk_tables_cap = 0;
+        CUDA_TRY(cudaMalloc(&st->d_chunk_tables, tbytes), "cudaMalloc(chunk work tables)");
+        st->chunk_tables_cap = tbytes;
+    }
+    // the previous call's kernels are done (it ended with both streams
+    // synchronized), so the tables can be overwritten
+    CUDA_TRY(cudaMemcpyAsync(st->d_chunk_tables, tables.data(), tbytes, cudaMemcpyHostToDevice, cs),
+             "cudaMemcpyAsync(chunk work tables)");
+    uint64_t host_off = 0;
+    bool recorded[mtgp_streams::kStages] = {};
+    for (size_t c = 0; c < works.size(); ++c) {
+        const int b = (int)(c % mtgp_streams::kStages);
+        if (recorded[b])
+            CUDA_TRY(cudaStreamWaitEvent(cs, st->ev_copy[b], 0), "cudaStreamWaitEvent");
+        mtgp_status s = launch_work_table(st, works[c], (char*)st->d_chunk_tables + toff[c], st->cfg,
+                                          st->stage[b], cs);
         if (s != MTGP_OK)
             return s;
         CUDA_TRY(cudaEventRecord(st->ev_gen[b], cs), "cudaEventRecord");
         CUDA_TRY(cudaStreamWaitEvent(st->copy_stream, st->ev_gen[b], 0), "cudaStreamWaitEvent");
-        CUDA_TRY(cudaMemcpyAsync((char*)host_out + host_off * 4, st->stage[b], fill * 4,
+        CUDA_TRY(cudaMemcpyAsync((char*)host_out + host_off * 4, st->stage[b], fills[c] * 4,
                                  cudaMemcpyDeviceToHost, st->copy_stream),
                  "cudaMemcpyAsync(D2H)");
         CUDA_TRY(cudaEventRecord(st->ev_copy[b], st->copy_stream), "cudaEventRecord");
         recorded[b] = true;
-        host_off += fill;
-        fill = 0;
-        cid.clear();
-        ccount.clear();
-        ++nchunk;
-        return MTGP_OK;
-    };
-    for (uint32_t j = 0; j < n_req; ++j) {
-        uint64_t left = counts[j];
-        while (left) {
-            const uint64_t take = std::min(left, chunk - fill);
-            cid.push_back(ids[j]);
-            ccount.push_back(take);
-            fill += take;
-            left -= take;
-            if (fill == chunk) {
-                mtgp_status s = flush();
-                if (s != MTGP_OK)
-                    return s;
-            }
-        }
+        host_off += fills[c];
     }
-    mtgp_status s = flush();
-    if (s != MTGP_OK)
-        return s;
     CUDA_TRY(cudaStreamSynchronize(st->copy_stream), "cudaStreamSynchronize(copy)");
     CUDA_TRY(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
     return ok();

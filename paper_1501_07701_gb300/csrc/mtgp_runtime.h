@@ -87,6 +87,10 @@ struct mtgp_streams {
     cudaEvent_t ev_gen[kStages] = {};
     cudaEvent_t ev_copy[kStages] = {};
     cudaStream_t copy_stream = nullptr;
+    // the work tables of every chunk of one device-to-host call, uploaded
+    // together before its first kernel
+    void* d_chunk_tables = nullptr;
+    size_t chunk_tables_cap = 0;
     // autotuning
     cudaStream_t tune_stream = nullptr;
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
@@ -182,6 +186,10 @@ mtgp_status launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, v
                         cudaStream_t s);
 mtgp_status launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w, const LaunchCfg& cfg,
                              void* out, cudaStream_t s);
+// Launches `w` from a work table already in device memory at `table`
+// (counters zeroed, laid out by table_bytes / fill_table).
+mtgp_status launch_work_table(mtgp_streams* st, const Work& w, void* table, const LaunchCfg& cfg,
+                              void* out, cudaStream_t s);
 void free_table_slot(TableSlot& s);
 mtgp_status validate_config(const mtgp_launch_config* c, LaunchCfg* out);
 // Number of leading (longest) items a launch hands to whole CTAs.
