@@ -509,14 +509,20 @@ def measure_fused_stats(mtgp, torch, st, ids, counts, out, stream, flush, gen_ra
     bounds = quality.default_hamming_bounds(1200, 4)
     total = int(counts.sum())
     saved = mtgp.mtgp_get_launch_config(st)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    piece = split_piece("auto", total, sms)
     by_res = {}
     try:
-        # 8 and 16 warps per SM (one or two 8-warp CTAs); the faster is reported
-        for ctas in (1, 2):
+        # 8 and 16 warps per SM (one or two 8-warp CTAs), and 16 with the longest
+        # requests split into pieces (stitched statistics); the fastest is reported
+        for label, ctas, max_piece in (("8", 1, 0), ("16", 2, 0), ("16 split %d" % piece, 2, piece),
+                                       ("16 split %d" % (piece // 2), 2, piece // 2)):
             mtgp.mtgp_set_launch_config(st, **dict(saved, warps_per_cta=8, ctas_per_sm=ctas))
             plan = mtgp.mtgp_plan_create(st, ids, counts, FORMATS["u32"], out)
             try:
                 mtgp.mtgp_plan_set_stats(plan, gap=(25, 5, 128), hamming=(25, 5, 1200, bounds))
+                if max_piece:
+                    mtgp.mtgp_plan_set_split(plan, max_piece)
             except mtgp.MtgpError as e:
                 return {"unavailable": str(e)}
             info = mtgp.mtgp_plan_get_info(plan)
@@ -536,9 +542,11 @@ def measure_fused_stats(mtgp, torch, st, ids, counts, out, stream, flush, gen_ra
             hist, tab = mtgp.mtgp_plan_read_stats(plan, stream)
             sh = mtgp.mtgp_gap_histogram(out, counts, r=25, b=5, t=128, stream=stream)
             stab = mtgp.mtgp_hamming_pairs(out, counts, r=25, s=5, L=1200, bounds=bounds, stream=stream)
-            by_res[8 * info["resident_ctas_per_sm"]] = {
+            by_res[label] = {
                 "gnum_s": total / (sum(ms) / len(ms) / 1e3) / 1e9,
-                "kernel_ms": [round(v, 3) for v in ms], "grid_ctas": info["grid_ctas"],
+                "launch_ms": [round(v, 3) for v in ms], "grid_ctas": info["grid_ctas"],
+                "warps_per_sm": 8 * info["resident_ctas_per_sm"], "max_piece": info["max_piece"],
+                "jumps_per_launch": info["n_jumps"], "kernel_launches": info["kernel_launches"],
                 "regs_per_thread": info["regs_per_thread"],
                 "counts_equal_standalone": bool(np.array_equal(hist, sh) and np.array_equal(tab, stab)),
                 "pooled": (hist.sum(axis=0), tab.sum(axis=0))}
@@ -551,8 +559,8 @@ def measure_fused_stats(mtgp, torch, st, ids, counts, out, stream, flush, gen_ra
     for v in by_res.values():
         v.pop("pooled", None)
     return {"gnum_s": b["gnum_s"], "generation_alone_gnum_s": gen_rate, "ratio": b["gnum_s"] / gen_rate,
-            "warps_per_sm": best, "steps": steps, "kernel": "mtgp_fused_kernel",
-            "by_warps_per_sm": {str(k): v for k, v in sorted(by_res.items())},
+            "best": best, "steps": steps, "kernel": "mtgp_fused_kernel",
+            "by_launch_shape": by_res,
             "counts_equal_standalone": all(v["counts_equal_standalone"] for v in by_res.values()),
             "pooled_gap": quality.gap_test(hs, b=5),
             "pooled_hamming": quality.hamming_test(ts, L=1200, bounds=bounds)}

@@ -1317,6 +1317,8 @@ static mtgp_status record_graph(mtgp_plan* p)
         if (e2 == cudaSuccess)
             e2 = launch_fused(p->stats_fn, a, p->sa, dim3(p->stats_geo.grid), dim3(p->stats_geo.threads),
                               p->stats_geo.smem, cap);
+        if (e2 == cudaSuccess && split)
+            e2 = launch_stats_stitch(a.segs, p->d_piece_start, p->d_pieces, p->n_req, p->sa, cap);
     } else if (e2 == cudaSuccess) {
         e2 = launch_generate(a, p->geo, cap);
     }
@@ -1336,7 +1338,8 @@ static mtgp_status record_graph(mtgp_plan* p)
         return fail_cuda(e3, "cudaStreamEndCapture");
     p->graph = graph;
     CUDA_TRY(cudaGraphInstantiate(&p->exec, graph, 0), "cudaGraphInstantiate");
-    p->kernel_launches = 1 + (n_copies ? 1u : 0u) + (n_jumps ? 1u : 0u) + (n_backs ? 1u : 0u);
+    p->kernel_launches = 1 + (n_copies ? 1u : 0u) + (n_jumps ? 1u : 0u) + (n_backs ? 1u : 0u) +
+                         (p->stats && split && p->n_req ? 1u : 0u);
     return MTGP_OK;
 }
 
@@ -1432,6 +1435,64 @@ static mtgp_status build_launch(mtgp_plan* p, uint64_t max_piece)
     return geometry_for(st, p->cfg, p->n_items, &p->geo);
 }
 
+static void free_split_stats(mtgp_plan* p)
+{
+    if (p->d_req_base)
+        cudaFree(p->d_req_base);
+    if (p->d_seg_stats)
+        cudaFree(p->d_seg_stats);
+    if (p->d_piece_start)
+        cudaFree(p->d_piece_start);
+    if (p->d_pieces)
+        cudaFree(p->d_pieces);
+    p->d_req_base = nullptr;
+    p->d_seg_stats = nullptr;
+    p->d_piece_start = nullptr;
+    p->d_pieces = nullptr;
+    p->sa.req_base = nullptr;
+    p->sa.seg_stats = nullptr;
+}
+
+// The tables a split plan's statistics need (none for an unsplit plan):
+// each request's first output index, one edge record per launched segment,
+// and each request's segments ordered by their position in the request.
+static mtgp_status build_split_stats(mtgp_plan* p)
+{
+    free_split_stats(p);
+    if (!p->stats || !p->split.max_piece || p->n_req == 0)
+        return MTGP_OK;
+    std::vector<unsigned long long> base(p->n_req, 0ull);
+    for (const Segment& sg : p->work.segs)   // unsplit: one segment per request, at its start
+        base[sg.req] = sg.out_off;
+    const std::vector<Segment>& segs = p->split.work.segs;
+    std::vector<uint32_t> start(p->n_req + 1u, 0u), order(segs.size());
+    for (const Segment& sg : segs)
+        ++start[sg.req + 1u];
+    for (uint32_t j = 0; j < p->n_req; ++j)
+        start[j + 1u] += start[j];
+    std::vector<uint32_t> fillp(start.begin(), start.end() - 1);
+    for (uint32_t k = 0; k < (uint32_t)segs.size(); ++k)
+        order[fillp[segs[k].req]++] = k;
+    for (uint32_t j = 0; j < p->n_req; ++j)
+        std::sort(order.begin() + start[j], order.begin() + start[j + 1u],
+                  [&](uint32_t a, uint32_t b) { return segs[a].out_off < segs[b].out_off; });
+    CUDA_TRY(cudaMalloc(&p->d_req_base, base.size() * 8u), "cudaMalloc(request offsets)");
+    CUDA_TRY(cudaMemcpy(p->d_req_base, base.data(), base.size() * 8u, cudaMemcpyHostToDevice),
+             "cudaMemcpy(request offsets)");
+    CUDA_TRY(cudaMalloc(&p->d_seg_stats, std::max<size_t>(segs.size(), 1) * sizeof(SegStat)),
+             "cudaMalloc(piece records)");
+    CUDA_TRY(cudaMalloc(&p->d_piece_start, start.size() * 4u), "cudaMalloc(piece lists)");
+    CUDA_TRY(cudaMemcpy(p->d_piece_start, start.data(), start.size() * 4u, cudaMemcpyHostToDevice),
+             "cudaMemcpy(piece lists)");
+    CUDA_TRY(cudaMalloc(&p->d_pieces, std::max<size_t>(order.size(), 1) * 4u), "cudaMalloc(pieces)");
+    if (!order.empty())
+        CUDA_TRY(cudaMemcpy(p->d_pieces, order.data(), order.size() * 4u, cudaMemcpyHostToDevice),
+                 "cudaMemcpy(pieces)");
+    p->sa.req_base = p->d_req_base;
+    p->sa.seg_stats = p->d_seg_stats;
+    return MTGP_OK;
+}
+
 // Kernel and launch geometry of a plan's fused statistics: G = 8 warps per
 // CTA, as many resident CTAs per SM as the plan's configuration asks warps
 // per SM (warps_per_cta x ctas_per_sm / 8, at least 1; occupancy maximum when
@@ -1494,6 +1555,7 @@ static void destroy_plan(mtgp_plan* p)
         cudaFree(p->d_hist);
     if (p->d_tab)
         cudaFree(p->d_tab);
+    free_split_stats(p);
     free_split(p);
     delete p;
 }
@@ -1670,11 +1732,11 @@ extern "C" mtgp_status mtgp_plan_set_split(mtgp_plan_t p, uint64_t max_piece)
         return fail(MTGP_EINVAL, "null plan");
     if (max_piece != 0 && max_piece < 64)
         return fail(MTGP_EINVAL, "max_piece %llu below 64", (unsigned long long)max_piece);
-    if (max_piece != 0 && p->stats)
-        return fail(MTGP_EINVAL, "the plan computes statistics per request: its requests cannot be split");
     DeviceGuard g(p->st->device);
     mtgp_status r = build_launch(p, max_piece);
     if (r != MTGP_OK)
+        return r;
+    if (p->stats && ((r = stats_geometry(p)) != MTGP_OK || (r = build_split_stats(p)) != MTGP_OK))
         return r;
     r = record_graph(p);
     if (r != MTGP_OK)
@@ -1717,8 +1779,6 @@ extern "C" mtgp_status mtgp_plan_set_stats(mtgp_plan_t p, const mtgp_stats_confi
         for (uint32_t i = 0; i < c->n_bounds; ++i)
             a.bounds[i] = c->bounds[i];
     }
-    if ((gap || ham) && p->split.max_piece)
-        return fail(MTGP_EINVAL, "statistics per request need an unsplit plan");
     if ((gap || ham) && p->d_trace)
         return fail(MTGP_EINVAL, "statistics: turn the plan's trace off first");
     if (gap || ham)
@@ -1757,7 +1817,10 @@ extern "C" mtgp_status mtgp_plan_set_stats(mtgp_plan_t p, const mtgp_stats_confi
     } else {
         p->sa = StatsArgs{};
     }
-    mtgp_status r = record_graph(p);
+    mtgp_status r = build_split_stats(p);
+    if (r != MTGP_OK)
+        return r;
+    r = record_graph(p);
     if (r != MTGP_OK)
         return r;
     return ok();

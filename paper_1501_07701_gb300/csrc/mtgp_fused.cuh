@@ -37,6 +37,15 @@
 // smaller K take the per-sub-step form (K >= 32: at most one block end per
 // sub-step).
 //
+// Split launches: a request may be cut into pieces (segments of different
+// items) that different warps generate.  A piece that does not start its
+// request leaves its first gap (whose start lies in an earlier piece) and
+// the block pair open at its start uncounted; it records them, with its
+// trailing run of non-visits and the weights of the pair open at its end,
+// in one SegStat, and the stitch kernel completes them in request order.
+// Until both are settled the piece's rows take the slow path, so the full
+// rows' loop is the same as for unsplit launches.
+//
 // Ballots, shuffles and reductions run in warp-uniform control flow.
 #pragma once
 
@@ -44,10 +53,13 @@
 
 namespace mtgp {
 
-// The warp's running statistics of its current request (all fields but acc
+// The warp's running statistics of its current piece (all fields but acc
 // and bnd are uniform across the warp).
 struct StatsState {
-    uint32_t seq;    // current request (index in the launch), kNoSeq = none
+    uint32_t seq;    // current segment (index in the launch), kNoSeq = none
+    uint32_t req;    // its request
+    uint32_t lead;   // bit 0: the piece's first visit is still ahead; bit 1: the pair open at its start
+                     // has not ended (pieces that do not start their request)
     uint32_t D;      // gap test: non-visits since the last visit (< 2^31)
     uint32_t rem;    // Hamming: values left in the current block, 1 .. K
     uint32_t half;   // Hamming: 1 when the current block is its pair's second
@@ -86,11 +98,52 @@ __device__ __forceinline__ uint32_t gap_run(uint32_t o, bool valid, uint32_t l0,
     return in ? hs + 4u * min(gap, A.t) : own;
 }
 
+// The piece's edge words (4, after the pair table): [0] non-visits before
+// its first visit, [1] and [2] its weights in the blocks of the pair open at
+// its start.
+__device__ __forceinline__ uint32_t* piece_edges(uint32_t* tab, const StatsArgs& A)
+{
+    return tab + ((A.C * A.C + 3u) & ~3u);
+}
+
+// gap_run for the slow path, where a piece's first visit may come: its gap
+// begins in an earlier piece, so it is recorded (non-visits before it in
+// this piece) instead of counted.
+__device__ __forceinline__ uint32_t gap_run_piece(uint32_t o, bool valid, uint32_t l0, uint32_t n,
+                                                  uint32_t lane, uint32_t lower, StatsState& st, uint32_t hs,
+                                                  uint32_t own, uint32_t* tab, const StatsArgs& A)
+{
+    const bool in = valid && (o & A.gmask) == 0u;
+    const uint32_t B = __ballot_sync(MTGP_FULL, in);
+    const uint32_t hb = hibit(B & lower);
+    const uint32_t gap = hb != 0xFFFFFFFFu ? lane - hb - 1u : lane - l0 + st.D;
+    bool counted = in;
+    if ((st.lead & 1u) && B) {
+        const uint32_t f = (uint32_t)__ffs(B) - 1u;
+        if (lane == 0u)
+            piece_edges(tab, A)[0] = st.D + f - l0;
+        counted = in && lane != f;
+        st.lead &= ~1u;
+    }
+    st.D = B ? l0 + n - 1u - hibit(B) : st.D + n;
+    return counted ? hs + 4u * min(gap, A.t) : own;
+}
+
 // A Hamming block of weight W has ended: the first of a pair is kept, the
-// second completes the pair, which lane 0 counts in the warp's table.
+// second completes the pair, which lane 0 counts in the warp's table.  In
+// the pair open at a piece's start, the weights go to the piece's edges.
 __device__ __forceinline__ void block_done(uint32_t W, uint32_t lane, StatsState& st, uint32_t* tab,
                                            const StatsArgs& A)
 {
+    if (st.lead & 2u) {
+        if (lane == 0u)
+            piece_edges(tab, A)[1u + st.half] = W;
+        if (st.half)
+            st.lead &= ~2u;
+        st.wa = W;
+        st.half ^= 1u;
+        return;
+    }
     if (st.half) {
         const uint32_t ca = __popc(__ballot_sync(MTGP_FULL, st.bnd <= st.wa));
         const uint32_t cb = __popc(__ballot_sync(MTGP_FULL, st.bnd <= W));
@@ -118,31 +171,71 @@ __device__ __forceinline__ void ham_run(uint32_t w, uint32_t l0, uint32_t n, uin
     }
 }
 
-// Writes the current request's histogram and table rows (where the launch
-// asks for them) and starts request `next`.
+// Ends the current piece: records its edges (split launches) and adds its
+// histogram and table to its request's rows.  Then starts segment `next`
+// (kNoSeq: none): its position in its request sets where it stands in the
+// block pairs, and a piece that does not start its request begins with both
+// leads pending.
 __device__ __forceinline__ void stats_switch(StatsState& st, uint32_t next, uint32_t lane, uint32_t* h,
-                                             uint32_t* tab, const StatsArgs& A)
+                                             uint32_t* tab, const Segment* __restrict__ segs,
+                                             const StatsArgs& A)
 {
     if (st.seq == next)
         return;
+    uint32_t* pe = piece_edges(tab, A);
     if (st.seq != kNoSeq) {
+        if (A.seg_stats) {
+            const uint32_t part = __reduce_add_sync(MTGP_FULL, st.acc);   // the open block's weight here
+            __syncwarp();
+            if (lane == 0u) {
+                SegStat r;
+                const bool gl = (st.lead & 1u) != 0u, hl = (st.lead & 2u) != 0u;
+                r.gvisit = gl ? 0u : 1u;
+                r.gprefix = gl ? st.D : pe[0];
+                r.gsuffix = st.D;
+                if (hl) {   // the pair open at the start did not end here
+                    r.la = st.half ? pe[1] : part;
+                    r.lb = st.half ? part : 0u;
+                    r.ta = 0u;
+                    r.tb = 0u;
+                } else {
+                    r.la = pe[1];
+                    r.lb = pe[2];
+                    r.ta = st.half ? st.wa : part;
+                    r.tb = st.half ? part : 0u;
+                }
+                r.pad = 0u;
+                A.seg_stats[st.seq] = r;
+            }
+        }
         __syncwarp();
         for (uint32_t i = lane; i <= A.t; i += 32u) {
-            if (A.hist)
-                A.hist[(size_t)st.seq * (A.t + 1u) + i] = h[i];
+            if (A.hist && h[i])
+                atomicAdd(A.hist + (size_t)st.req * (A.t + 1u) + i, (unsigned long long)h[i]);
             h[i] = 0u;
         }
         for (uint32_t i = lane; i < A.C * A.C; i += 32u) {
-            if (A.tab)
-                A.tab[(size_t)st.seq * A.C * A.C + i] = tab[i];
+            if (A.tab && tab[i])
+                atomicAdd(A.tab + (size_t)st.req * A.C * A.C + i, (unsigned long long)tab[i]);
             tab[i] = 0u;
         }
-        __syncwarp();
     }
+    uint32_t pos = 0u;
+    st.lead = 0u;
+    if (next != kNoSeq) {
+        const Segment sg = segs[next];
+        st.req = sg.req;
+        const uint64_t off = A.req_base ? sg.out_off - A.req_base[sg.req] : 0ull;
+        pos = (uint32_t)(off % (2ull * A.K));
+        st.lead = (off ? 1u : 0u) | (pos ? 2u : 0u);
+        if (lane < 3u)
+            pe[lane] = 0u;
+    }
+    __syncwarp();
     st.seq = next;
     st.D = 0u;
-    st.rem = A.K;
-    st.half = 0u;
+    st.half = pos >= A.K ? 1u : 0u;
+    st.rem = A.K - pos % A.K;
     st.wa = 0u;
     st.acc = 0u;
 }
@@ -306,17 +399,17 @@ __device__ __forceinline__ void fused_row_slow(uint32_t (&r)[M], uint32_t* Sw, c
             o = of;
         else if (sg.fmt == 2)
             o = __float_as_uint(__uint_as_float(of) - 1.0f);
-        const uint32_t req = sg.req;
-        // statistics: runs of lanes of one request, in lane order
+        // statistics: runs of lanes of one segment, in lane order
         uint32_t remaining = __ballot_sync(MTGP_FULL, valid);
         while (remaining) {
             const uint32_t l0 = (uint32_t)__ffs(remaining) - 1u;
-            const uint32_t r0 = __shfl_sync(MTGP_FULL, req, l0);
-            const uint32_t same = __ballot_sync(MTGP_FULL, valid && req == r0) & remaining;
+            const uint32_t s0 = __shfl_sync(MTGP_FULL, s, l0);
+            const uint32_t same = __ballot_sync(MTGP_FULL, valid && s == s0) & remaining;
             const uint32_t n = (uint32_t)__popc(same);
             const bool in_run = (same >> lane) & 1u;
-            stats_switch(st, r0, lane, h, tab, A);
-            count_at(gap_run(o, in_run, l0, n, lane, lower, st, hist_addr(h), own_addr(h, lane, A), A));
+            stats_switch(st, s0, lane, h, tab, segs, A);
+            count_at(gap_run_piece(o, in_run, l0, n, lane, lower, st, hist_addr(h), own_addr(h, lane, A), tab,
+                                   A));
             ham_run(in_run ? __popc(o & A.hmask) : 0u, l0, n, lane, st, tab, A);
             remaining &= ~same;
         }
@@ -374,7 +467,14 @@ __device__ __forceinline__ void fused_item(const KParams& KP, const RowP& P, uin
         if (row + N <= seg_end) {
             const uint32_t nfull = (uint32_t)min((seg_end - row) / N, (uint64_t)0xFFFFFFFFu);
             uint32_t* ow = out + sg.out_off + (row - sg.g_start) + lane;
-            stats_switch(st, sg.req, lane, h, tab, A);
+            stats_switch(st, s, lane, h, tab, segs, A);
+            if (st.lead) {
+                // a piece whose first gap or first pair is still open: one row
+                // at a time on the slow path, which records them
+                fused_row_slow<M>(r, Sw, Q, P, lane, Tb, N, row, segs, s, s_end, out, st, h, tab, A);
+                row += N;
+                continue;
+            }
             if (A.K >= 128u) {
                 if (sg.fmt == 0)
                     fused_rows<M, 0, true>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
@@ -437,7 +537,7 @@ __global__ void __launch_bounds__(G * 32) mtgp_fused_kernel(const KParams P, uin
         h[i] = 0u;
     __syncthreads();
     const RowP R0 = {P.n, P.mask, P.pos, P.sh1, P.sh2, P.mirror};
-    StatsState st = {kNoSeq, 0u, A.K, 0u, 0u, 0u, 0xFFFFFFFFu};
+    StatsState st = {kNoSeq, 0u, 0u, 0u, A.K, 0u, 0u, 0u, 0xFFFFFFFFu};
 #pragma unroll
     for (uint32_t i = 0; i < 15u; ++i)
         if (lane == i && i + 1u < A.C)
@@ -472,7 +572,7 @@ __global__ void __launch_bounds__(G * 32) mtgp_fused_kernel(const KParams P, uin
                           tab, A);
         }
     }
-    stats_switch(st, kNoSeq, lane, h, tab, A);
+    stats_switch(st, kNoSeq, lane, h, tab, segs, A);
 }
 
 }  // namespace mtgp

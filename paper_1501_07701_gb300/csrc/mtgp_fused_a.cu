@@ -43,4 +43,69 @@ cudaError_t launch_fused(const void* fn, const GenArgs& a, const StatsArgs& A, d
     return cudaLaunchKernel(fn, grid, block, args, smem, s);
 }
 
+// One thread per request: walks the request's pieces in order and counts
+// what lies across their edges.  Gaps: the run of non-visits carried from
+// earlier pieces plus a piece's leading run is the gap of its first visit.
+// Pairs: the pair open at a piece's start holds pos = (its position in the
+// request) mod 2K values from earlier pieces; the piece adds its weights in
+// the pair's two blocks and, if the pair ends inside it (its length >= 2K -
+// pos), the completed pair is counted and the pair open at its end carries on.
+__global__ void __launch_bounds__(128) mtgp_stats_stitch_kernel(const Segment* __restrict__ segs,
+                                                               const uint32_t* __restrict__ piece_start,
+                                                               const uint32_t* __restrict__ pieces,
+                                                               uint32_t n_req, const StatsArgs A)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_req)
+        return;
+    const uint32_t p0 = piece_start[j], p1 = piece_start[j + 1u];
+    if (p1 - p0 < 2u)
+        return;
+    const uint64_t two_k = 2ull * A.K;
+    const SegStat f = A.seg_stats[pieces[p0]];
+    uint64_t run = f.gsuffix;
+    uint32_t wa = f.ta, wb = f.tb;
+    for (uint32_t q = p0 + 1u; q < p1; ++q) {
+        const uint32_t sidx = pieces[q];
+        const SegStat r = A.seg_stats[sidx];
+        const Segment sg = segs[sidx];
+        if (r.gvisit) {
+            const uint64_t gap = run + r.gprefix;
+            if (A.hist)
+                atomicAdd(A.hist + (size_t)j * (A.t + 1u) + (gap < A.t ? gap : (uint64_t)A.t), 1ull);
+            run = r.gsuffix;
+        } else {
+            run += r.gprefix;
+        }
+        const uint64_t pos = (sg.out_off - A.req_base[j]) % two_k;
+        if (pos == 0u) {
+            wa = r.ta;
+            wb = r.tb;
+            continue;
+        }
+        wa += r.la;
+        wb += r.lb;
+        if (sg.count >= two_k - pos) {
+            uint32_t ca = 0u, cb = 0u;
+            for (uint32_t i = 0; i + 1u < A.C && i < 15u; ++i) {
+                ca += A.bounds[i] <= wa;
+                cb += A.bounds[i] <= wb;
+            }
+            if (A.tab)
+                atomicAdd(A.tab + (size_t)j * A.C * A.C + ca * A.C + cb, 1ull);
+            wa = r.ta;
+            wb = r.tb;
+        }
+    }
+}
+
+cudaError_t launch_stats_stitch(const Segment* segs, const uint32_t* piece_start, const uint32_t* pieces,
+                                uint32_t n_req, const StatsArgs& A, cudaStream_t s)
+{
+    if (n_req == 0)
+        return cudaSuccess;
+    mtgp_stats_stitch_kernel<<<(n_req + 127u) / 128u, 128, 0, s>>>(segs, piece_start, pieces, n_req, A);
+    return cudaGetLastError();
+}
+
 }  // namespace mtgp

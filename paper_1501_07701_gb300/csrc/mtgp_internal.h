@@ -161,6 +161,18 @@ cudaError_t launch_gen_fn(const void* fn, const GenArgs& a, dim3 grid, dim3 bloc
 // Statistics of the paper's gap test (test 35) and Hamming-weight
 // independence test (test 100), Sec. 4.2, accumulated by the fused
 // generation kernel per request of its launch.
+// What one piece of a request (a segment of a split launch) leaves for the
+// stitch: its gap-test edges and its Hamming weights in the block pairs that
+// are open at its start and at its end.
+struct SegStat {
+    uint32_t gprefix;   // non-visits before the piece's first visit (its length if none)
+    uint32_t gsuffix;   // non-visits after its last visit (its length if none)
+    uint32_t gvisit;    // 1 if the piece has a visit
+    uint32_t la, lb;    // weights in blocks a and b of the pair open at the piece's start
+    uint32_t ta, tb;    // weights in blocks a and b of the pair open at its end
+    uint32_t pad;
+};
+
 struct StatsArgs {
     uint32_t gmask;                // gap test: the b bits after r dropped leading bits (0: off)
     uint32_t t;                    // gap lengths >= t pooled in class t (t + 1 counts)
@@ -168,17 +180,22 @@ struct StatsArgs {
     uint32_t K;                    // values per L-bit block (L / s), >= 32
     uint32_t C;                    // weight classes (n_bounds + 1), <= 16
     uint32_t bounds[15];           // class of weight w = number of bounds <= w
-    unsigned long long* hist;      // n_req x (t + 1) counts
-    unsigned long long* tab;       // n_req x C x C counts
+    unsigned long long* hist;      // n_req x (t + 1) counts, added to
+    unsigned long long* tab;       // n_req x C x C counts, added to
+    // split launches (null otherwise): each request's first output index
+    // (a segment's position in its request is out_off - req_base[req]) and
+    // one record per segment for the stitch
+    const unsigned long long* req_base;
+    SegStat* seg_stats;
 };
 
 // Shared-memory words per warp that the statistics add: the gap histogram
 // of the warp's current request (rounded up to 4 words), one slot per lane
-// that absorbs the counts of non-visiting lanes, and the request's C x C
-// pair table (rounded up to 4 words).
+// that absorbs the counts of non-visiting lanes, the request's C x C pair
+// table (rounded up to 4 words) and 4 words of the current piece's edges.
 __host__ __device__ inline uint32_t stats_smem_words(uint32_t t, uint32_t C)
 {
-    return ((t + 1u + 3u) & ~3u) + 32u + ((C * C + 3u) & ~3u);
+    return ((t + 1u + 3u) & ~3u) + 32u + ((C * C + 3u) & ~3u) + 4u;
 }
 
 // The fused generation kernel (single-warp items, 128-word pipelined steps,
@@ -188,5 +205,10 @@ __host__ __device__ inline uint32_t stats_smem_words(uint32_t t, uint32_t C)
 const void* fused_kernel_ptr(int M, int G);
 cudaError_t launch_fused(const void* fn, const GenArgs& a, const StatsArgs& A, dim3 grid, dim3 block,
                          size_t smem, cudaStream_t s);
+// Completes the statistics of split requests from their pieces' records:
+// request j's pieces are segs[pieces[piece_start[j] ..  piece_start[j+1])],
+// in request order (requests with one piece have none listed).
+cudaError_t launch_stats_stitch(const Segment* segs, const uint32_t* piece_start, const uint32_t* pieces,
+                                uint32_t n_req, const StatsArgs& A, cudaStream_t s);
 
 }  // namespace mtgp

@@ -168,6 +168,12 @@ struct mtgp_plan {
     mtgp::Geometry stats_geo{};
     unsigned long long* d_hist = nullptr;
     unsigned long long* d_tab = nullptr;
+    // split plans with statistics: each request's first output index, one
+    // edge record per launched segment, and each request's pieces in order
+    unsigned long long* d_req_base = nullptr;
+    mtgp::SegStat* d_seg_stats = nullptr;
+    uint32_t* d_piece_start = nullptr;
+    uint32_t* d_pieces = nullptr;
 };
 
 namespace mtgp {

@@ -9,7 +9,9 @@ positions and widths (mask at the top, at the bottom, one bit), t from 1 to
 1023, the block length down to its minimum of 32 values, 0 to 15 class
 bounds, requests of 0, 1, < N, = N and many rows, several requests per
 stream, plan replays, every format, per-stream parameter sets, the three
-state sizes and autotuning; then the refusals.
+state sizes and autotuning; split plans, whose requests are counted in
+pieces and stitched, with piece lengths around the state size and the
+Hamming pair length; then the refusals.
 """
 import os
 
@@ -64,19 +66,29 @@ def _oracle_stats(ref, counts, gap, hamming):
     return (np.array(hs) if gap else None), (np.array(ts) if hamming else None)
 
 
-def _run(st, op, ids, counts, fmt, gap, hamming, reps=2, cfg=None, autotune=False, sets=None):
+def _run(st, op, ids, counts, fmt, gap, hamming, reps=2, cfg=None, autotune=False, sets=None, split=0,
+         split_first=False):
     """Launches a statistics plan `reps` times; checks outputs, states and
-    statistics against the oracle after every launch."""
+    statistics against the oracle after every launch.  split: piece length
+    of a split plan (set before or after the statistics)."""
     total = int(counts.sum())
     out = torch.full((total + 4,), -1, dtype=torch.int32, device="cuda")
     if cfg:
         mtgp.mtgp_set_launch_config(st, **cfg)
     plan = mtgp.mtgp_plan_create(st, ids, counts, fmt, out[:total])
+    if split and split_first:
+        mtgp.mtgp_plan_set_split(plan, split)
     mtgp.mtgp_plan_set_stats(plan, gap=gap, hamming=hamming)
+    if split and not split_first:
+        mtgp.mtgp_plan_set_split(plan, split)
     if autotune:
         mtgp.mtgp_plan_autotune(plan)
     info = mtgp.mtgp_plan_get_info(plan)
-    assert info["stats"] and info["kernel_launches"] == 1
+    assert info["stats"]
+    if split:
+        assert info["n_split_streams"] > 0 and info["max_piece"] == split
+    else:
+        assert info["kernel_launches"] == 1
     states = mtgp.mtgp_get_statuses(st)
     for rep in range(reps):
         # the statistics are rewritten by every launch
@@ -179,6 +191,54 @@ def test_fused_stats_launch_shapes(cfg):
     assert info["config"]["warps_per_cta"] == 8
 
 
+SPLIT_CASES = [
+    (64, PAPER["gap"], PAPER["hamming"]),
+    (350, (0, 1, 7), (0, 1, 32, [])),
+    (351, (20, 10, 1023), (27, 5, 160, [10, 12, 14, 16, 18])),
+    (480, PAPER["gap"], PAPER["hamming"]),
+    (1000, (31, 1, 1), (31, 1, 50, list(range(10, 40, 2))[:15])),
+    (4096, PAPER["gap"], (25, 5, 1200, [590, 600, 610])),
+    (33333, PAPER["gap"], PAPER["hamming"]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SPLIT_CASES)))
+def test_fused_stats_split_plans(case):
+    """Requests cut into pieces on several warps: the pieces' counts and the
+    stitched edges equal the oracle's counts of the whole requests."""
+    max_piece, gap, hamming = SPLIT_CASES[case]
+    gp = mtgp.mtgp_params_generate(11213, workloads.PARAM_SEED)
+    op = oracle.params_generate(11213, workloads.PARAM_SEED)
+    rng = np.random.default_rng(500 + case)
+    n = 24
+    ids, counts = _requests(rng, n, 12, op.n, 120000)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(n, dtype=np.uint32))
+    _run(st, op, ids, counts, mtgp.MTGP_U32, gap, hamming, split=max_piece, split_first=case % 2 == 0)
+
+
+@pytest.mark.parametrize("mexp", [23209, 44497])
+def test_fused_stats_split_larger_states(mexp):
+    gp = mtgp.mtgp_params_generate(mexp, workloads.PARAM_SEED)
+    op = oracle.params_generate(mexp, workloads.PARAM_SEED)
+    rng = np.random.default_rng(mexp + 1)
+    ids, counts = _requests(rng, 10, 5, op.n, 300000)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(10, dtype=np.uint32))
+    _run(st, op, ids, counts, mtgp.MTGP_F32_01, **PAPER, split=50000)
+
+
+def test_fused_stats_split_sets_autotune_16_warps():
+    set_seeds = [workloads.PARAM_SEED + 7 + k for k in range(3)]
+    gsets = [mtgp.mtgp_params_generate(11213, k) for k in set_seeds]
+    osets = [oracle.params_generate(11213, k) for k in set_seeds]
+    n = 16
+    set_of = (np.arange(n) % 3).astype(np.uint32)
+    st = mtgp.mtgp_init_statuses_multi(gsets, set_of, np.arange(n, dtype=np.uint32))
+    rng = np.random.default_rng(9)
+    ids, counts = _requests(rng, n, 8, osets[0].n, 200000)
+    _run(st, osets[0], ids, counts, mtgp.MTGP_U32, reps=1, autotune=True, sets=(osets, set_of),
+         cfg=dict(warps_per_cta=8, ctas_per_sm=2, words_per_lane=4, kernel=0), split=20000, **PAPER)
+
+
 def test_fused_counts_equal_standalone_kernels():
     """The fused counts equal the standalone reductions over the output."""
     gp = mtgp.mtgp_params_generate(11213, workloads.PARAM_SEED)
@@ -221,12 +281,12 @@ def test_fused_stats_off_and_refusals():
     mtgp.mtgp_plan_set_trace(plan, True)
     refused(mtgp.mtgp_plan_set_stats, plan, **PAPER)
     mtgp.mtgp_plan_set_trace(plan, False)
-    mtgp.mtgp_plan_set_split(plan, 1000)
-    refused(mtgp.mtgp_plan_set_stats, plan, **PAPER)
-    mtgp.mtgp_plan_set_split(plan, 0)
     mtgp.mtgp_plan_set_stats(plan, **PAPER)
-    refused(mtgp.mtgp_plan_set_split, plan, 1000)
     refused(mtgp.mtgp_plan_set_trace, plan, True)
+    # a split plan computes statistics too (stitched); removing the split keeps them
+    mtgp.mtgp_plan_set_split(plan, 1000)
+    assert mtgp.mtgp_plan_get_info(plan)["stats"]
+    mtgp.mtgp_plan_set_split(plan, 0)
     # turning the statistics off returns the plan to the plain kernel
     mtgp.mtgp_plan_set_stats(plan)
     info = mtgp.mtgp_plan_get_info(plan)
