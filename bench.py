@@ -502,8 +502,10 @@ def quality_stats(mtgp, torch, out, counts, stream):
 def measure_fused_stats(mtgp, torch, st, ids, counts, out, stream, flush, gen_rate, steps=5):
     """Generation with both statistics fused in (mtgp_plan_set_stats, the
     parameters of quality_stats): per-launch rate over `steps` launches
-    (CUDA events, the L2 rewrite between launches as in the timed region),
-    next to generation alone timed the same way; the fused counts of the last
+    (CUDA events, the L2 rewrite between launches as in the timed region)
+    at 8 and 16 warps per SM, and at 16 with the longest requests split into
+    pieces of two lengths (statistics stitched across pieces), next to
+    generation alone timed the same way.  Each shape's counts of its last
     launch are compared with the standalone reductions over its output."""
     from paper_1501_07701_gb300 import quality
     bounds = quality.default_hamming_bounds(1200, 4)

@@ -320,10 +320,16 @@ typedef struct {
  * would over the plan's output buffer, request j being sequence j.  The
  * counts are accumulated by a generation kernel of its own while the
  * outputs are still in registers, so the outputs are not read back from
- * memory; mtgp_plan_read_stats returns them.  cfg = NULL (or both tests
- * left out) returns the plan to the plain generation kernel.
- * MTGP_EINVAL: parameters out of range; a split plan or one with tracing
- * on; a request of 2^31 numbers or more; a parameter set with N - pos < 256
+ * memory; mtgp_plan_read_stats returns them.  In a split plan
+ * (mtgp_plan_set_split, before or after this call) a request's pieces are
+ * counted by the warps that generate them; each piece records the run of
+ * non-visits before its first visit and after its last, and its weights in
+ * the block pairs open at its start and end, and a stitch kernel in the same
+ * launch counts what lies across the pieces' edges.  The counts are the
+ * same as for the unsplit plan.  cfg = NULL (or both tests left out)
+ * returns the plan to the plain generation kernel.
+ * MTGP_EINVAL: parameters out of range; a plan with tracing on; a request
+ * of 2^31 numbers or more; a parameter set with N - pos < 256
  * or a state size without an instantiation of the fused kernel (the
  * exponents whose ceil(N/32) is 10, 11, 20, 22, 23 or 44, e.g. 11213, 23209
  * and 44497).  Re-records the plan's graph; synchronous.  No counterpart in
