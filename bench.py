@@ -458,13 +458,17 @@ def run_ours(args, rank, world, local_rank):
 
 
 def split_piece(spec: str, total: int, sms: int) -> int:
-    """Piece length for --split: 0 (off), an explicit count, or 'auto' --
-    the numbers per warp slot at 16 warps per SM, so that no piece outlasts
-    an even share of the launch at that residency."""
+    """Piece length for --split: 0 (off), an explicit count, 'auto' -- the
+    numbers per warp slot at 16 warps per SM, so that no piece outlasts an
+    even share of the launch at that residency -- or 'autoW', the launch cut
+    into W pieces per SM (for short states, whose best residency is higher:
+    'auto48' is half a warp slot's share at 24 warps per SM)."""
     if spec in ("", "0"):
         return 0
     if spec == "auto":
         return max(64, -(-total // (sms * 16)))
+    if spec.startswith("auto"):
+        return max(64, -(-total // (sms * int(spec[4:]))))
     return max(64, int(spec))
 
 
@@ -829,7 +833,8 @@ EXTRA_CONFIGS = [("single stream x 2^20, Mexp 11213, u32", "single", "u32", "0",
     ("long 1024 x 2^20, Mexp %d, %s" % (m, f), "long%d" % m, f, "0", 0)
     for m in (23209, 44497) for f in ("u32", "f12", "f01")] + [
     ("uneven 10 000 streams, Mexp 3217, u32", "uneven", "u32", "0", 3217),
-    ("uneven 10 000 streams, Mexp 3217, u32, split at 16 warps per SM", "uneven", "u32", "auto", 3217)]
+    ("uneven 10 000 streams, Mexp 3217, u32, split in pieces of total / (48 x SMs)", "uneven", "u32",
+     "auto48", 3217)]
 
 
 def measure_configs(mtgp, torch, dev, stream, flush, steps=5, warmup=3):
@@ -1007,7 +1012,7 @@ def main():
     ap.add_argument("--split", default="0",
                     help="cut streams longer than this many numbers into pieces started by exact "
                          "jumps (mtgp_plan_set_split); 'auto' = the numbers per warp slot at 16 warps "
-                         "per SM; 0 = off")
+                         "per SM; 'autoW' = the launch cut into W pieces per SM; 0 = off")
     ap.add_argument("--ranks", dest="rank_split", default="weak", choices=["weak", "strong"],
                     help="N > 1: weak = one workload instance per GPU; strong = one instance cut "
                          "into contiguous stream ranges")

@@ -1092,9 +1092,10 @@ std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
 {
     // Residency matters as much as block shape: a launch whose longest
     // streams dominate runs best with few warps per SM (each stream gets a
-    // larger share of the SM), an even launch with many.  Candidates cover
-    // 4 .. 24 warps per SM, with and without the whole-CTA mode for long
-    // streams.
+    // larger share of the SM), an even launch with many (short states, whose
+    // 64-word steps leave much latency to hide, gain up to 32 warps per SM).
+    // Candidates cover 4 .. 32 warps per SM and the occupancy maximum, with
+    // and without the whole-CTA mode for long streams.
     std::vector<LaunchCfg> v;
     auto add = [&](int w, int k, int cap, int coop) {
         if (!fast_supported(P, k, w))
@@ -1114,6 +1115,8 @@ std::vector<LaunchCfg> mtgp::tuning_candidates(const KParams& P)
             add(2, k, cap, 0);
         add(8, k, 1, 0);
         add(8, k, 2, 0);
+        add(8, k, 3, 0);
+        add(8, k, 4, 0);
         add(8, k, 0, 0);
         if (k >= 4)
             add(4, k, 0, 100);

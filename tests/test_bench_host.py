@@ -66,3 +66,13 @@ def test_oracle_rate_counts_whole_streams(generator):
     assert rate > 0 and secs > 0 and 1 <= streams <= 40
     order = np.random.default_rng(0).permutation(40)[:streams]
     assert numbers == int(w["counts"][order].sum())
+
+
+def test_split_piece_specs():
+    total, sms = 5121292474, 152
+    assert bench.split_piece("0", total, sms) == 0 and bench.split_piece("", total, sms) == 0
+    assert bench.split_piece("auto", total, sms) == -(-total // (sms * 16)) == 2105795
+    assert bench.split_piece("auto48", total, sms) == -(-total // (sms * 48))
+    assert bench.split_piece("16384", total, sms) == 16384
+    assert bench.split_piece("10", total, sms) == 64          # the smallest piece the library takes
+    assert bench.split_piece("auto48", 1000, sms) == 64
