@@ -1811,10 +1811,16 @@ extern "C" mtgp_status mtgp_plan_set_stats(mtgp_plan_t p, const mtgp_stats_confi
     p->d_tab = nullptr;
     if (p->stats) {
         const size_t nr = std::max<uint32_t>(p->n_req, 1u);
-        if (gap)
+        // zeroed here too: a plan with no work never launches, and its
+        // counts read back before a launch are zeros
+        if (gap) {
             CUDA_TRY(cudaMalloc(&p->d_hist, nr * (a.t + 1u) * 8u), "cudaMalloc(gap histograms)");
-        if (ham)
+            CUDA_TRY(cudaMemset(p->d_hist, 0, nr * (a.t + 1u) * 8u), "cudaMemset(gap histograms)");
+        }
+        if (ham) {
             CUDA_TRY(cudaMalloc(&p->d_tab, nr * a.C * a.C * 8u), "cudaMalloc(Hamming tables)");
+            CUDA_TRY(cudaMemset(p->d_tab, 0, nr * a.C * a.C * 8u), "cudaMemset(Hamming tables)");
+        }
         p->sa.hist = p->d_hist;
         p->sa.tab = p->d_tab;
     } else {

@@ -239,6 +239,20 @@ def test_fused_stats_split_sets_autotune_16_warps():
          cfg=dict(warps_per_cta=8, ctas_per_sm=2, words_per_lane=4, kernel=0), split=20000, **PAPER)
 
 
+def test_fused_stats_plan_without_work():
+    """Requests of zero numbers: no launch runs, and the counts read back are zeros."""
+    gp = mtgp.mtgp_params_generate(11213, workloads.PARAM_SEED)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(3, dtype=np.uint32))
+    out = torch.empty(4, dtype=torch.int32, device="cuda")
+    plan = mtgp.mtgp_plan_create(st, [0, 1, 2], [0, 0, 0], mtgp.MTGP_U32, out)
+    mtgp.mtgp_plan_set_stats(plan, **PAPER)
+    mtgp.mtgp_plan_launch(plan)
+    torch.cuda.synchronize()
+    hist, tab = mtgp.mtgp_plan_read_stats(plan)
+    assert hist.shape == (3, 129) and not hist.any()
+    assert tab.shape == (3, 4, 4) and not tab.any()
+
+
 def test_fused_counts_equal_standalone_kernels():
     """The fused counts equal the standalone reductions over the output."""
     gp = mtgp.mtgp_params_generate(11213, workloads.PARAM_SEED)
