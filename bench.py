@@ -946,8 +946,10 @@ def measure_serving(mtgp, torch, args):
     """Continuous batching vs one launch per request: on the serving trace
     (50 000 requests/s, which overloads the one-launch-per-request arm), and
     on a trace at a rate that arm sustains (its latencies are then service
-    times, not backlog).  Each arm's host time per launch (work-table build,
-    upload and kernel launch) is reported beside its latencies."""
+    times, not backlog).  A third arm batches continuously with requests
+    longer than --serving-piece numbers cut into pieces started by exact
+    jumps (config max_piece).  Each arm's host time per launch (work-table
+    build, upload and kernel launch) is reported beside its latencies."""
     rate_lo, secs_lo = 20000.0, min(5.0, args.serving_seconds)
     traces = [("offered_50k_req_s", workloads.serving_trace(duration_s=args.serving_seconds),
                50000.0, args.serving_seconds),
@@ -957,21 +959,32 @@ def measure_serving(mtgp, torch, args):
     params = mtgp.mtgp_params_generate(workloads.MEXP_MAIN, workloads.PARAM_SEED)
     st = mtgp.mtgp_init_statuses(params, np.arange(n_streams, dtype=np.uint32))
     srv = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4)
+    srv_split = None
+    if args.serving_piece:
+        srv_split = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4,
+                                            max_piece=args.serving_piece)
     res = {"workload": "65536 resident Mexp 11213 streams; Poisson arrivals (seed 11); "
-                       "k = floor(2^U), U~U[8,20]; u32 or f32[0,1); arena (admission cap) 8 GiB"}
+                       "k = floor(2^U), U~U[8,20]; u32 or f32[0,1); arena (admission cap) 8 GiB",
+           "split_piece": args.serving_piece}
+    arms = [(srv, 0, "continuous_batching"), (srv, 1, "one_launch_per_request")]
+    if srv_split:
+        arms.append((srv_split, 0, "continuous_batching_split"))
     for key, tr, rate, secs in traces:
         r = {"rate_req_s": rate, "seconds": secs, "requests": int(tr["t"].size),
              "offered_gnum_s": float(tr["counts"].sum()) / secs / 1e9}
-        for mode, name in [(0, "continuous_batching"), (1, "one_launch_per_request")]:
-            lat, _, stats = mtgp.mtgp_server_run_trace(srv, tr["t"], tr["ids"], tr["counts"],
+        for server, mode, name in arms:
+            lat, _, stats = mtgp.mtgp_server_run_trace(server, tr["t"], tr["ids"], tr["counts"],
                                                        tr["fmt"], mode=mode)
             r[name] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
                        "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                        "mean_ms": 1e3 * float(lat.mean()),
                        "gnum_s": stats["numbers"] / stats["elapsed"] / 1e9,
                        "kernel_launches": int(stats["ticks"]), "elapsed_s": stats["elapsed"],
-                       "host_us_per_launch": 1e6 * stats["launch_host_s"] / max(1, stats["ticks"])}
+                       "host_us_per_launch": 1e6 * stats["launch_host_s"] / max(1, stats["ticks"]),
+                       "jumps": int(stats["jumps"])}
         res[key] = r
+    if srv_split:
+        srv_split.close()
     srv.close()
     st.close()
     if not args.no_serving_parity:
@@ -997,6 +1010,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the serving trace (0 = skip the serving measurement)")
+    ap.add_argument("--serving-piece", type=int, default=1 << 16,
+                    help="serving arm with requests longer than this cut into pieces started by "
+                         "jumps (server max_piece; 0 = no such arm)")
     ap.add_argument("--config", default="",
                     help="force warps_per_cta,words_per_lane,coop_percent[,ctas_per_sm[,kernel]] "
                          "(skips autotuning)")

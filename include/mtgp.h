@@ -380,7 +380,18 @@ mtgp_status mtgp_plan_free(mtgp_plan_t plan);
  * requests are coalesced into a tick, one kernel launch; up to max_inflight
  * ticks run at once on separate CUDA streams.  Requests for one stream
  * complete in submission order and produce exactly the numbers a lone
- * request sequence would. */
+ * request sequence would.
+ *
+ * With cfg.max_piece (Sec. 1 and 2: sub-streams of one generator), a tick
+ * takes either requests longer than max_piece or shorter ones.  The long
+ * requests' streams are cut into pieces of max_piece numbers (at most 64; a
+ * longer stream gets 64 equal pieces), each started by an exact jump and
+ * advanced by its own warp, so that a long request completes in about a
+ * piece's time plus a jump's; short requests never wait for jumps.  The
+ * jump polynomials of the offsets j * max_piece (j < 64) are computed when
+ * the server is created and kept on the device (handles with one parameter
+ * set); other offsets and per-stream sets compute theirs on first use
+ * (cached). */
 
 typedef struct {
     uint64_t arena_bytes;        /* device output arena = admission cap (0 = 8 GiB) */
@@ -389,6 +400,10 @@ typedef struct {
     double   tick_timeout_s;     /* longest wait for one launch's completion before
                                     progress / run_trace return MTGP_ETIMEOUT,
                                     seconds > 0 (0 = 60)                           */
+    uint64_t max_piece;          /* requests longer than this are cut into pieces
+                                    started by exact jumps, as in a split plan,
+                                    and ticks take either such requests or
+                                    shorter ones (0 = never; else >= 64)           */
 } mtgp_server_config;
 
 typedef struct {
@@ -409,6 +424,7 @@ typedef struct {
     double   busy_wait;          /* seconds the loop idled while requests were queued */
     double   launch_host_s;      /* host seconds spent building work tables and
                                     issuing launches (table upload + kernel)      */
+    uint64_t jumps;              /* pieces started by jumps (max_piece > 0)       */
 } mtgp_server_stats;
 
 /* Creates a server over `streams` (kept by reference; must outlive the

@@ -781,7 +781,7 @@ mtgp_status mtgp::launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& 
 // Uploads a work table through `sl` (waiting for the slot's previous
 // consumer) and launches on `s`; records the slot's event after the kernel.
 mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w,
-                                   const LaunchCfg& cfg, void* out, cudaStream_t s)
+                                   const LaunchCfg& cfg, void* out, cudaStream_t s, const RowArray* rows)
 {
     if (w.items.empty())
         return MTGP_OK;
@@ -807,7 +807,7 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
     fill_table(w, sl.host);
     CUDA_TRY(cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, s),
              "cudaMemcpyAsync(work table)");
-    mtgp_status stt = launch_work_table(st, w, sl.dev, cfg, out, s);
+    mtgp_status stt = launch_work_table(st, w, sl.dev, cfg, out, s, rows);
     if (stt != MTGP_OK)
         return stt;
     CUDA_TRY(cudaEventRecord(sl.ev, s), "cudaEventRecord");
@@ -816,7 +816,7 @@ mtgp_status mtgp::launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& 
 }
 
 mtgp_status mtgp::launch_work_table(mtgp_streams* st, const Work& w, void* table, const LaunchCfg& cfg,
-                                    void* out, cudaStream_t s)
+                                    void* out, cudaStream_t s, const RowArray* rows)
 {
     if (w.items.empty())
         return MTGP_OK;
@@ -840,6 +840,11 @@ mtgp_status mtgp::launch_work_table(mtgp_streams* st, const Work& w, void* table
     a.trace = nullptr;
     a.sets = st->d_sets;
     a.set_of = st->d_set_of;
+    if (rows) {
+        a.states = rows->states;
+        a.n_streams = rows->n_rows;
+        a.set_of = rows->set_of;
+    }
     CUDA_TRY(launch_generate(a, g, s), "generation kernel launch");
     return MTGP_OK;
 }

@@ -190,12 +190,20 @@ LaunchCfg default_config(const KParams& P);
 mtgp_status geometry_for(mtgp_streams* st, const LaunchCfg& cfg, uint32_t n_items, Geometry* g);
 mtgp_status launch_work(mtgp_streams* st, const Work& w, const LaunchCfg& cfg, void* out,
                         cudaStream_t s);
+// A launch's own state rows (a split launch: one row per item, see
+// SplitWork) in place of the handle's states; set_of: each row's parameter
+// set index (handles with one set per stream), else null.
+struct RowArray {
+    uint32_t* states;
+    uint32_t n_rows;
+    const uint32_t* set_of;
+};
 mtgp_status launch_work_slot(mtgp_streams* st, TableSlot& sl, const Work& w, const LaunchCfg& cfg,
-                             void* out, cudaStream_t s);
+                             void* out, cudaStream_t s, const RowArray* rows = nullptr);
 // Launches `w` from a work table already in device memory at `table`
 // (counters zeroed, laid out by table_bytes / fill_table).
 mtgp_status launch_work_table(mtgp_streams* st, const Work& w, void* table, const LaunchCfg& cfg,
-                              void* out, cudaStream_t s);
+                              void* out, cudaStream_t s, const RowArray* rows = nullptr);
 void free_table_slot(TableSlot& s);
 mtgp_status validate_config(const mtgp_launch_config* c, LaunchCfg* out);
 // Number of leading (longest) items a launch hands to whole CTAs.

@@ -29,6 +29,13 @@
 
 #include "mtgp_runtime.h"
 
+#define CUDA_TRY_S(call, what)               \
+    do {                                     \
+        cudaError_t e_ = (call);             \
+        if (e_ != cudaSuccess)               \
+            return fail_cuda(e_, what);      \
+    } while (0)
+
 using namespace mtgp;
 
 namespace {
@@ -101,11 +108,24 @@ struct Req {
     bool live;
 };
 
+// Device buffers of a tick whose long requests are split (config
+// max_piece): the launch's own state rows, and one table of row copies
+// (stream -> row, row -> stream), row parameter sets, jump items and jump
+// polynomials, assembled on the host and uploaded in one copy.
+struct TickSplit {
+    uint32_t* rows = nullptr;
+    size_t rows_cap = 0;   // words
+    char* aux = nullptr;
+    size_t aux_cap = 0;    // bytes
+    std::vector<char> host;
+};
+
 struct Tick {
     std::vector<uint32_t> reqs;
     cudaStream_t cs = nullptr;
     cudaEvent_t ev = nullptr;
     TableSlot slot;
+    TickSplit sp;
     bool busy = false;
     double t_launch = 0;   // steady-clock seconds at launch
 };
@@ -131,6 +151,15 @@ struct mtgp_server {
     bool keep_results = false;          // trace mode with recorded offsets
     bool hold = false;                  // diagnostic: completions read as not ready
     double launch_host_s = 0;           // host time in work-table builds and launches
+    std::vector<uint32_t> set_of_stream; // per-stream parameter set (handles with one per stream)
+    uint64_t n_jumps = 0;               // pieces started by jumps
+    // jump polynomials of the piece offsets j * max_piece, j = 1 .. 63, on
+    // the device (handles with one parameter set): a tick's jumps then need
+    // only their items
+    uint32_t* d_polys = nullptr;
+    uint32_t poly_words = 0;
+    size_t jump_smem = 0;
+    std::vector<uint32_t> poly_deg;     // degree of polynomial j - 1
 };
 
 // Completion query of one event, bounded by the server's deadline.  Returns
@@ -164,6 +193,10 @@ static void destroy_server(mtgp_server* s)
         free_table_slot(t.slot);
         if (t.slot.ev)
             cudaEventDestroy(t.slot.ev);
+        if (t.sp.rows)
+            cudaFree(t.sp.rows);
+        if (t.sp.aux)
+            cudaFree(t.sp.aux);
         if (t.ev)
             cudaEventDestroy(t.ev);
         if (t.cs)
@@ -171,6 +204,8 @@ static void destroy_server(mtgp_server* s)
     }
     if (s->arena)
         cudaFree(s->arena);
+    if (s->d_polys)
+        cudaFree(s->d_polys);
     delete s;
 }
 
@@ -195,6 +230,8 @@ extern "C" mtgp_status mtgp_server_create(mtgp_streams_t st, const mtgp_server_c
             return fail(MTGP_EINVAL, "max_inflight %u > 64", c.max_inflight);
         if (!(c.tick_timeout_s > 0))
             return fail(MTGP_EINVAL, "tick_timeout_s must be positive");
+        if (c.max_piece != 0 && c.max_piece < 64)
+            return fail(MTGP_EINVAL, "max_piece %llu below 64", (unsigned long long)c.max_piece);
         DeviceGuard g(st->device);
         mtgp_server* s = new mtgp_server;
         s->st = st;
@@ -208,6 +245,45 @@ extern "C" mtgp_status mtgp_server_create(mtgp_streams_t st, const mtgp_server_c
             return fail_cuda(e, "cudaMalloc(arena)");
         }
         s->alloc.reset(c.arena_bytes / 4);
+        if (c.max_piece) {
+            if (st->d_sets) {
+                s->set_of_stream.resize(st->n_streams);
+                e = cudaMemcpy(s->set_of_stream.data(), st->d_set_of, st->n_streams * 4u,
+                               cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) {
+                    destroy_server(s);
+                    return fail_cuda(e, "cudaMemcpy(set index)");
+                }
+            } else {
+                // the jump polynomials of the piece offsets j * max_piece
+                // (j < 64) are computed once here rather than in a tick
+                std::vector<uint32_t> rows(63, 0u), sets(63, 0u);
+                std::vector<uint64_t> lens(63);
+                for (uint32_t j = 0; j < 63u; ++j)
+                    lens[j] = (uint64_t)(j + 1u) * c.max_piece;
+                JumpBatch jb;
+                mtgp_status r = build_jump_batch(st, rows, sets, lens, &jb);
+                if (r != MTGP_OK) {
+                    destroy_server(s);
+                    return r;
+                }
+                // one polynomial per offset, in offset order (the batch lists
+                // distinct lengths once, sorted)
+                s->poly_deg.assign(63, 0u);
+                for (const JumpItem& ji : jb.items)
+                    s->poly_deg[ji.poly] = ji.deg;
+                s->poly_words = jb.words;
+                s->jump_smem = jb.smem;
+                e = cudaMalloc(&s->d_polys, jb.poly_words.size() * 4u);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(s->d_polys, jb.poly_words.data(), jb.poly_words.size() * 4u,
+                                   cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) {
+                    destroy_server(s);
+                    return fail_cuda(e, "jump polynomials");
+                }
+            }
+        }
         for (Tick& t : s->ticks) {
             if ((e = cudaStreamCreateWithFlags(&t.cs, cudaStreamNonBlocking)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming)) != cudaSuccess ||
@@ -310,6 +386,96 @@ static mtgp_status reap(mtgp_server* s, int* n_reaped)
 
 // Admits pending requests into one free tick slot and launches it.  Sets
 // *launched to 1 if a tick went out.
+// Launches the tick's work with its items longer than max_piece cut into
+// pieces (split_work): every item gets a row of the tick's own state array,
+// the rows of later pieces are advanced by exact jumps, the generation
+// kernel runs over the rows, and the unsplit items' rows and each split
+// item's last piece become the streams' new states.  All on the tick's
+// stream, in that order.
+static mtgp_status launch_split_tick(mtgp_server* s, Tick& t, const Work& w)
+{
+    mtgp_streams* st = s->st;
+    SplitWork sw;
+    mtgp_status r = split_work(w, s->cfg.max_piece, 64, s->set_of_stream, &sw);
+    if (r != MTGP_OK)
+        return r;
+    // jumps by j * max_piece (j < 64) take the server's device polynomials;
+    // others (streams cut into 64 equal pieces, per-stream parameter sets)
+    // get a batch of their own
+    JumpBatch jb;
+    bool cached = s->d_polys != nullptr;
+    for (size_t i = 0; cached && i < sw.jump_lens.size(); ++i)
+        cached = sw.jump_lens[i] % s->cfg.max_piece == 0 && sw.jump_lens[i] / s->cfg.max_piece <= 63u;
+    if (cached) {
+        for (size_t i = 0; i < sw.jump_rows.size(); ++i) {
+            const uint32_t j = (uint32_t)(sw.jump_lens[i] / s->cfg.max_piece) - 1u;
+            JumpItem ji;
+            ji.stream = sw.jump_rows[i];
+            ji.poly = j;
+            ji.deg = s->poly_deg[j];
+            ji.set = 0;
+            jb.items.push_back(ji);
+        }
+        jb.words = s->poly_words;
+        jb.smem = s->jump_smem;
+    } else {
+        r = build_jump_batch(st, sw.jump_rows, sw.jump_sets, sw.jump_lens, &jb);
+        if (r != MTGP_OK)
+            return r;
+    }
+    const uint32_t N = st->P.k.n, np = st->P.k.np;
+    const size_t rows_words = (size_t)sw.n_rows * np;
+    if (rows_words > t.sp.rows_cap) {
+        if (t.sp.rows)
+            cudaFree(t.sp.rows);
+        t.sp.rows = nullptr;
+        t.sp.rows_cap = 0;
+        const size_t cap = std::max<size_t>(rows_words * 2, (size_t)64 * np);
+        CUDA_TRY_S(cudaMalloc(&t.sp.rows, cap * 4u), "cudaMalloc(tick rows)");
+        t.sp.rows_cap = cap;
+    }
+    auto al = [](size_t x) { return (x + 15u) & ~(size_t)15u; };
+    const size_t b_copies = sw.copies.size() * sizeof(uint2), b_backs = sw.backs.size() * sizeof(uint2);
+    const size_t b_set = st->d_sets ? sw.row_set.size() * 4u : 0u;
+    const size_t b_ji = jb.items.size() * sizeof(JumpItem), b_poly = jb.poly_words.size() * 4u;
+    const size_t o_backs = al(b_copies), o_set = o_backs + al(b_backs), o_ji = o_set + al(b_set);
+    const size_t o_poly = o_ji + al(b_ji), total = o_poly + b_poly;
+    t.sp.host.resize(total);
+    std::memcpy(t.sp.host.data(), sw.copies.data(), b_copies);
+    std::memcpy(t.sp.host.data() + o_backs, sw.backs.data(), b_backs);
+    if (b_set)
+        std::memcpy(t.sp.host.data() + o_set, sw.row_set.data(), b_set);
+    if (b_ji)
+        std::memcpy(t.sp.host.data() + o_ji, jb.items.data(), b_ji);
+    if (b_poly)
+        std::memcpy(t.sp.host.data() + o_poly, jb.poly_words.data(), b_poly);
+    if (total > t.sp.aux_cap) {
+        if (t.sp.aux)
+            cudaFree(t.sp.aux);
+        t.sp.aux = nullptr;
+        t.sp.aux_cap = 0;
+        const size_t cap = std::max<size_t>(total * 2, 1u << 16);
+        CUDA_TRY_S(cudaMalloc(&t.sp.aux, cap), "cudaMalloc(tick split tables)");
+        t.sp.aux_cap = cap;
+    }
+    CUDA_TRY_S(cudaMemcpyAsync(t.sp.aux, t.sp.host.data(), total, cudaMemcpyHostToDevice, t.cs),
+               "cudaMemcpyAsync(tick split tables)");
+    CUDA_TRY_S(launch_copy_rows(st->d_states, t.sp.rows, (const uint2*)t.sp.aux, (uint32_t)sw.copies.size(),
+                                N, np, t.cs), "row copy");
+    const uint32_t* polys = cached ? s->d_polys : (const uint32_t*)(t.sp.aux + o_poly);
+    CUDA_TRY_S(launch_jump_batch(st, t.sp.rows, (const JumpItem*)(t.sp.aux + o_ji), (uint32_t)jb.items.size(),
+                                 polys, jb.words, jb.smem, t.cs),
+               "jump kernel");
+    RowArray ra{t.sp.rows, sw.n_rows, st->d_sets ? (const uint32_t*)(t.sp.aux + o_set) : nullptr};
+    r = launch_work_slot(st, t.slot, sw.work, st->cfg, s->arena, t.cs, &ra);
+    if (r != MTGP_OK)
+        return r;
+    CUDA_TRY_S(launch_copy_rows(t.sp.rows, st->d_states, (const uint2*)(t.sp.aux + o_backs),
+                                (uint32_t)sw.backs.size(), N, np, t.cs), "row copy back");
+    s->n_jumps += jb.items.size();
+    return MTGP_OK;
+}
+
 static mtgp_status admit_and_launch(mtgp_server* s, int* launched)
 {
     *launched = 0;
@@ -331,13 +497,21 @@ static mtgp_status admit_and_launch(mtgp_server* s, int* launched)
     std::vector<uint32_t> ids;
     std::vector<uint64_t> counts, offs;
     std::vector<int32_t> fmts;
+    // With max_piece, a tick takes either requests longer than it (split,
+    // started by jumps) or shorter ones, so that short requests never wait
+    // for a tick's jumps; the first request admitted sets the class.
+    bool tick_long = false;
     for (auto it = s->pending.begin(); it != s->pending.end();) {
         Req& r = s->reqs[*it];
-        if (s->busy[r.stream] || s->blocked[r.stream] == s->epoch) {
+        const bool is_long = s->cfg.max_piece && r.count > s->cfg.max_piece;
+        if (s->busy[r.stream] || s->blocked[r.stream] == s->epoch ||
+            (!t->reqs.empty() && is_long != tick_long)) {
             s->blocked[r.stream] = s->epoch;   // keeps this stream's later requests behind it
             ++it;
             continue;
         }
+        if (t->reqs.empty())
+            tick_long = is_long;
         if (t->reqs.size() >= s->cfg.max_tick_requests)
             break;
         uint64_t off;
@@ -361,7 +535,10 @@ static mtgp_status admit_and_launch(mtgp_server* s, int* launched)
                                 (uint32_t)ids.size(), 0, w, offs.data());
     if (st != MTGP_OK)
         return st;
-    st = launch_work_slot(s->st, t->slot, w, s->st->cfg, s->arena, t->cs);
+    if (s->cfg.max_piece && w.max_item > s->cfg.max_piece)
+        st = launch_split_tick(s, *t, w);
+    else
+        st = launch_work_slot(s->st, t->slot, w, s->st->cfg, s->arena, t->cs);
     if (st != MTGP_OK)
         return st;
     cudaError_t e = cudaEventRecord(t->ev, t->cs);
@@ -572,7 +749,7 @@ extern "C" mtgp_status mtgp_server_run_trace(mtgp_server_t s, const double* t_ar
         for (const Tick& t : s->ticks)
             if (t.busy)
                 return fail(MTGP_EBUSY, "server has ticks in flight");
-        const uint64_t ticks0 = s->n_ticks, nums0 = s->n_numbers, reqs0 = s->n_requests;
+        const uint64_t ticks0 = s->n_ticks, nums0 = s->n_numbers, reqs0 = s->n_requests, jumps0 = s->n_jumps;
         const double launch0 = s->launch_host_s;
         double busy_wait = 0;
         const double t0 = now_s();
@@ -625,6 +802,7 @@ extern "C" mtgp_status mtgp_server_run_trace(mtgp_server_t s, const double* t_ar
             stats->elapsed = t1 - t0 - (n ? t_arrival[0] : 0);
             stats->busy_wait = busy_wait;
             stats->launch_host_s = s->launch_host_s - launch0;
+            stats->jumps = s->n_jumps - jumps0;
         }
         if (rc != MTGP_OK)
             return rc;

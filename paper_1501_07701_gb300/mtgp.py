@@ -72,7 +72,8 @@ class MtParams(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
-                ("max_tick_requests", ctypes.c_uint32), ("tick_timeout_s", ctypes.c_double)]
+                ("max_tick_requests", ctypes.c_uint32), ("tick_timeout_s", ctypes.c_double),
+                ("max_piece", ctypes.c_uint64)]
 
 
 class Completion(ctypes.Structure):
@@ -84,7 +85,8 @@ class Completion(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_uint64), ("numbers", ctypes.c_uint64),
                 ("ticks", ctypes.c_uint64), ("elapsed", ctypes.c_double),
-                ("busy_wait", ctypes.c_double), ("launch_host_s", ctypes.c_double)]
+                ("busy_wait", ctypes.c_double), ("launch_host_s", ctypes.c_double),
+                ("jumps", ctypes.c_uint64)]
 
 
 _VP = ctypes.c_void_p
@@ -535,8 +537,8 @@ class Server:
 
 
 def mtgp_server_create(streams: Streams, arena_bytes=0, max_inflight=0, max_tick_requests=0,
-                       tick_timeout_s=0.0):
-    c = ServerConfig(arena_bytes, max_inflight, max_tick_requests, tick_timeout_s)
+                       tick_timeout_s=0.0, max_piece=0):
+    c = ServerConfig(arena_bytes, max_inflight, max_tick_requests, tick_timeout_s, max_piece)
     h = _VP()
     _call("mtgp_server_create", streams.handle, ctypes.byref(c), ctypes.byref(h))
     return Server(h, streams)
@@ -595,7 +597,7 @@ def mtgp_server_run_trace(server: Server, t_arrival, ids, counts, fmts, mode=0, 
           _p64(offs) if record else None, ctypes.byref(st))
     return lat, offs, {"requests": st.requests, "numbers": st.numbers, "ticks": st.ticks,
                        "elapsed": st.elapsed, "busy_wait": st.busy_wait,
-                       "launch_host_s": st.launch_host_s}
+                       "launch_host_s": st.launch_host_s, "jumps": st.jumps}
 
 
 # ---------------------------------------------------------------------------

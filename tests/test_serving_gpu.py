@@ -78,6 +78,63 @@ def test_trace_results_equal_alone(mode):
         assert stats["ticks"] < len(tr["t"])   # requests were coalesced
 
 
+@pytest.mark.parametrize("max_piece", [64, 351, 5000])
+def test_split_ticks_equal_alone(max_piece):
+    """Ticks whose long requests are cut into pieces started by jumps: every
+    result and final state equals the oracle's request-by-request replay."""
+    tr = _small_trace(n_req=1500, n_streams=200, seed=8)
+    st, op, states0 = _setup(tr["n_streams"])
+    total = int(tr["counts"].sum())
+    arena = 4 * (total + 64 * len(tr["t"]))
+    srv = mtgp.mtgp_server_create(st, arena_bytes=arena, max_inflight=4, max_piece=max_piece)
+    lat, offs, stats = mtgp.mtgp_server_run_trace(srv, tr["t"], tr["ids"], tr["counts"], tr["fmt"],
+                                                  mode=0, record=True)
+    assert stats["requests"] == len(tr["t"]) and stats["jumps"] > 0
+    arena_host = _arena_view(srv, arena // 4)
+    ref, ref_states = _replay_oracle(op, states0, tr["ids"], tr["counts"], tr["fmt"])
+    for j in range(len(ref)):
+        got = arena_host[int(offs[j]):int(offs[j]) + int(tr["counts"][j])]
+        assert np.array_equal(got, ref[j]), "request %d (stream %d)" % (j, tr["ids"][j])
+    assert np.array_equal(mtgp.mtgp_get_statuses(st), ref_states)
+
+
+def test_split_ticks_per_stream_sets_submit_progress():
+    """submit / progress with split ticks on a handle with one parameter set per stream."""
+    set_seeds = [workloads.PARAM_SEED + 3 + k for k in range(3)]
+    gsets = [mtgp.mtgp_params_generate(workloads.MEXP_MAIN, k) for k in set_seeds]
+    osets = [oracle.params_generate(workloads.MEXP_MAIN, k) for k in set_seeds]
+    n = 12
+    set_of = (np.arange(n) % 3).astype(np.uint32)
+    st = mtgp.mtgp_init_statuses_multi(gsets, set_of, np.arange(n, dtype=np.uint32))
+    states = mtgp.mtgp_get_statuses(st)
+    rng = np.random.default_rng(21)
+    ids = rng.integers(0, n, 40).astype(np.uint32)
+    counts = rng.integers(1, 30000, 40).astype(np.uint64)
+    fmts = rng.integers(0, 3, 40).astype(np.int32)
+    srv = mtgp.mtgp_server_create(st, arena_bytes=4 * (int(counts.sum()) + 4096), max_piece=4000)
+    for j in range(40):
+        mtgp.mtgp_server_submit(srv, ids[j], counts[j], fmts[j], j)
+    done = {}
+    while len(done) < 40:
+        for c in mtgp.mtgp_server_progress(srv):
+            done[c["tag"]] = c
+    arena = mtgp.mtgp_server_read(srv, 0, int(counts.sum()) + 4096)
+    for j in range(40):
+        ref, states[ids[j]] = oracle.generate(osets[set_of[ids[j]]], states[ids[j]], int(counts[j]),
+                                              int(fmts[j]))
+        c = done[j]
+        assert np.array_equal(arena[c["arena_offset"]:c["arena_offset"] + c["count"]], ref), j
+        mtgp.mtgp_server_release(srv, c["arena_offset"], c["count"])
+    assert np.array_equal(mtgp.mtgp_get_statuses(st), states)
+
+
+def test_split_ticks_reject_tiny_pieces():
+    st, _, _ = _setup(4)
+    with pytest.raises(mtgp.MtgpError) as ei:
+        mtgp.mtgp_server_create(st, arena_bytes=1 << 20, max_piece=63)
+    assert ei.value.status == 1
+
+
 def test_submit_progress_with_small_arena():
     st, op, states0 = _setup(16)
     rng = np.random.default_rng(9)
