@@ -898,12 +898,12 @@ def measure_configs(mtgp, torch, dev, stream, flush, steps=5, warmup=3):
     return res
 
 
-def verify_serving_prefix(mtgp, tr, n_streams, budget=1_200_000_000):
+def verify_serving_prefix(mtgp, tr, n_streams, budget=1_200_000_000, max_piece=0):
     """Replays the prefix of the serving trace whose results fit the 8 GiB
-    arena at once, through continuous batching, recording every result's
-    arena offset; then checks every request of the prefix against the
-    oracle's replay of its stream's requests alone and in order, and every
-    final state."""
+    arena at once, through continuous batching (split ticks when max_piece),
+    recording every result's arena offset; then checks every request of the
+    prefix against the oracle's replay of its stream's requests alone and in
+    order, and every final state."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     cum = np.cumsum(tr["counts"].astype(np.int64))
@@ -912,7 +912,7 @@ def verify_serving_prefix(mtgp, tr, n_streams, budget=1_200_000_000):
     params = mtgp.mtgp_params_generate(workloads.MEXP_MAIN, workloads.PARAM_SEED)
     st = mtgp.mtgp_init_statuses(params, np.arange(n_streams, dtype=np.uint32))
     states0 = mtgp.mtgp_get_statuses(st)
-    srv = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4)
+    srv = mtgp.mtgp_server_create(st, arena_bytes=8 << 30, max_inflight=4, max_piece=max_piece)
     _, offs, _ = mtgp.mtgp_server_run_trace(srv, t, ids, counts, fmts, mode=0, record=True)
     arena = mtgp.mtgp_server_read(srv, 0, int((offs + counts).max()))
     op = oracle.params_generate(workloads.MEXP_MAIN, workloads.PARAM_SEED)
@@ -989,6 +989,9 @@ def measure_serving(mtgp, torch, args):
     st.close()
     if not args.no_serving_parity:
         res["parity_prefix"] = verify_serving_prefix(mtgp, traces[0][1], n_streams)
+        if args.serving_piece:
+            res["parity_prefix_split"] = verify_serving_prefix(mtgp, traces[0][1], n_streams,
+                                                               max_piece=args.serving_piece)
     return res
 
 
