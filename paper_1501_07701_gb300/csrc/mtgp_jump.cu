@@ -790,16 +790,17 @@ static std::vector<const Poly*> jump_polys(const SetP& p, const Poly& mu, const 
 
 mtgp_status mtgp::build_jump_batch(mtgp_streams* st, const std::vector<uint32_t>& rows,
                                    const std::vector<uint32_t>& sets, const std::vector<uint64_t>& jumps,
-                                   JumpBatch* out)
+                                   JumpBatch* out, const std::vector<KSet>* given_sets)
 {
     out->items.clear();
     out->poly_words.clear();
     out->words = 0;
     out->smem = 0;
-    std::vector<KSet> host_sets;
-    if (st->d_sets) {
-        host_sets.resize(st->n_sets);
-        const cudaError_t e = cudaMemcpy(host_sets.data(), st->d_sets, st->n_sets * sizeof(KSet),
+    std::vector<KSet> own_sets;
+    const std::vector<KSet>& host_sets = given_sets ? *given_sets : own_sets;
+    if (st->d_sets && !given_sets) {
+        own_sets.resize(st->n_sets);
+        const cudaError_t e = cudaMemcpy(own_sets.data(), st->d_sets, st->n_sets * sizeof(KSet),
                                          cudaMemcpyDeviceToHost);
         if (e != cudaSuccess)
             return fail_cuda(e, "cudaMemcpy(parameter sets)");

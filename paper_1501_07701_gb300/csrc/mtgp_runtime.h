@@ -222,9 +222,11 @@ mtgp_status split_work(const Work& w, uint64_t max_piece, uint32_t max_pieces,
 
 // Jump polynomials and items for advancing rows[i] (of the array the launch
 // is given) by jumps[i] numbers (0 = no jump); sets[i] = parameter set index.
+// host_sets: a host copy of the handle's per-stream parameter sets (null:
+// read from the device when needed).
 mtgp_status build_jump_batch(mtgp_streams* st, const std::vector<uint32_t>& rows,
                              const std::vector<uint32_t>& sets, const std::vector<uint64_t>& jumps,
-                             JumpBatch* out);
+                             JumpBatch* out, const std::vector<KSet>* host_sets = nullptr);
 cudaError_t launch_jump_batch(const mtgp_streams* st, uint32_t* rows_base, const JumpItem* d_items,
                               uint32_t n, const uint32_t* d_polys, uint32_t words, size_t smem,
                               cudaStream_t s);

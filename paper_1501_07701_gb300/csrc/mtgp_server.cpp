@@ -152,6 +152,7 @@ struct mtgp_server {
     bool hold = false;                  // diagnostic: completions read as not ready
     double launch_host_s = 0;           // host time in work-table builds and launches
     std::vector<uint32_t> set_of_stream; // per-stream parameter set (handles with one per stream)
+    std::vector<KSet> host_sets;        // those sets, for the ticks' jump polynomials
     uint64_t n_jumps = 0;               // pieces started by jumps
     // jump polynomials of the piece offsets j * max_piece, j = 1 .. 63, on
     // the device (handles with one parameter set): a tick's jumps then need
@@ -248,8 +249,12 @@ extern "C" mtgp_status mtgp_server_create(mtgp_streams_t st, const mtgp_server_c
         if (c.max_piece) {
             if (st->d_sets) {
                 s->set_of_stream.resize(st->n_streams);
+                s->host_sets.resize(st->n_sets);
                 e = cudaMemcpy(s->set_of_stream.data(), st->d_set_of, st->n_streams * 4u,
                                cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(s->host_sets.data(), st->d_sets, st->n_sets * sizeof(KSet),
+                                   cudaMemcpyDeviceToHost);
                 if (e != cudaSuccess) {
                     destroy_server(s);
                     return fail_cuda(e, "cudaMemcpy(set index)");
@@ -419,7 +424,8 @@ static mtgp_status launch_split_tick(mtgp_server* s, Tick& t, const Work& w)
         jb.words = s->poly_words;
         jb.smem = s->jump_smem;
     } else {
-        r = build_jump_batch(st, sw.jump_rows, sw.jump_sets, sw.jump_lens, &jb);
+        r = build_jump_batch(st, sw.jump_rows, sw.jump_sets, sw.jump_lens, &jb,
+                             st->d_sets ? &s->host_sets : nullptr);
         if (r != MTGP_OK)
             return r;
     }
