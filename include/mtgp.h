@@ -329,10 +329,11 @@ typedef struct {
  * same as for the unsplit plan.  cfg = NULL (or both tests left out)
  * returns the plan to the plain generation kernel.
  * MTGP_EINVAL: parameters out of range; a plan with tracing on; a request
- * of 2^31 numbers or more; a parameter set with N - pos < 256
- * or a state size without an instantiation of the fused kernel (the
- * exponents whose ceil(N/32) is 10, 11, 20, 22, 23 or 44, e.g. 11213, 23209
- * and 44497).  Re-records the plan's graph; synchronous.  No counterpart in
+ * of 2^31 numbers or more; a state size without an instantiation of the
+ * fused kernel (ceil(N/32) of 4, 5, 10, 11, 20, 22, 23 or 44: e.g. Mexp
+ * 3217, 4253, 11213, 23209 and 44497); a parameter set with N - pos < 256
+ * (< 32 for ceil(N/32) of 4 or 5, whose rows are counted one 32-column
+ * sub-step at a time).  Re-records the plan's graph; synchronous.  No counterpart in
  * the paper beyond the tests' definitions: it fuses the paper's quality
  * measurements into generation. */
 mtgp_status mtgp_plan_set_stats(mtgp_plan_t plan, const mtgp_stats_config* cfg);

@@ -1516,8 +1516,10 @@ static mtgp_status stats_geometry(mtgp_plan* p)
     const void* fn = fused_kernel_ptr(M, G);
     if (!fn)
         return fail(MTGP_EINVAL, "statistics: no fused kernel for N = %u (ceil(N/32) = %d)", P.n, M);
-    if (P.n - P.pos < 256u)
-        return fail(MTGP_EINVAL, "statistics: N - pos = %u below 256", P.n - P.pos);
+    // 128-word pipelined rows need N - pos >= 256; short states (M < 9) run
+    // every row one 32-column sub-step at a time, which needs N - pos >= 32
+    if (M >= 9 ? P.n - P.pos < 256u : P.n - P.pos < 32u)
+        return fail(MTGP_EINVAL, "statistics: N - pos = %u below %u", P.n - P.pos, M >= 9 ? 256u : 32u);
     Geometry g{};
     g.kernel = 0;
     g.k = 4;

@@ -46,6 +46,12 @@
 // Until both are settled the piece's rows take the slow path, so the full
 // rows' loop is the same as for unsplit launches.
 //
+// Short states (M < 9, e.g. Mexp 3217: N = 101, N - pos 64 .. 99) take the
+// slow path for every row: it advances one 32-column sub-step at a time,
+// reading each sub-step's words before writing them, which is exact while
+// N - pos >= 32 (a wrapped pick-up of column c then lands on a column below
+// the sub-step, already written).
+//
 // Ballots, shuffles and reductions run in warp-uniform control flow.
 #pragma once
 
@@ -468,14 +474,16 @@ __device__ __forceinline__ void fused_item(const KParams& KP, const RowP& P, uin
             const uint32_t nfull = (uint32_t)min((seg_end - row) / N, (uint64_t)0xFFFFFFFFu);
             uint32_t* ow = out + sg.out_off + (row - sg.g_start) + lane;
             stats_switch(st, s, lane, h, tab, segs, A);
-            if (st.lead) {
-                // a piece whose first gap or first pair is still open: one row
-                // at a time on the slow path, which records them
+            if (M < 9 || st.lead) {
+                // short states (no 128-word pipelined step fits), or a piece
+                // whose first gap or first pair is still open: one row at a
+                // time on the slow path, one 32-column sub-step after another
                 fused_row_slow<M>(r, Sw, Q, P, lane, Tb, N, row, segs, s, s_end, out, st, h, tab, A);
                 row += N;
                 continue;
             }
-            if (A.K >= 128u) {
+            if constexpr (M < 9) {
+            } else if (A.K >= 128u) {
                 if (sg.fmt == 0)
                     fused_rows<M, 0, true>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
                 else if (sg.fmt == 1)

@@ -239,6 +239,18 @@ def test_fused_stats_split_sets_autotune_16_warps():
          cfg=dict(warps_per_cta=8, ctas_per_sm=2, words_per_lane=4, kernel=0), split=20000, **PAPER)
 
 
+@pytest.mark.parametrize("mexp,split", [(3217, 0), (3217, 20000), (4253, 0)])
+def test_fused_stats_short_states(mexp, split):
+    """The paper's exponent (N = 101, N - pos < 128) and 4253 (N = 133): every
+    row is counted one 32-column sub-step at a time; unsplit and split."""
+    gp = mtgp.mtgp_params_generate(mexp, workloads.PARAM_SEED)
+    op = oracle.params_generate(mexp, workloads.PARAM_SEED)
+    rng = np.random.default_rng(mexp + split)
+    ids, counts = _requests(rng, 20, 10, op.n, 150000)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(20, dtype=np.uint32))
+    _run(st, op, ids, counts, mtgp.MTGP_U32, **PAPER, split=split)
+
+
 def test_fused_stats_plan_without_work():
     """Requests of zero numbers: no launch runs, and the counts read back are zeros."""
     gp = mtgp.mtgp_params_generate(11213, workloads.PARAM_SEED)
@@ -309,8 +321,8 @@ def test_fused_stats_off_and_refusals():
     torch.cuda.synchronize()
     ref, states = oracle.generate_many(op, states, ids, counts, 0, THREADS)
     _same(out.cpu().numpy().view(np.uint32), ref, "outputs after statistics off")
-    # short states (Mexp 3217, N - pos < 256) have no fused kernel
-    g3 = mtgp.mtgp_params_generate(3217, workloads.PARAM_SEED)
-    s3 = mtgp.mtgp_init_statuses(g3, np.arange(2, dtype=np.uint32))
-    p3 = mtgp.mtgp_plan_create(s3, [0, 1], [1000, 1000], mtgp.MTGP_U32, out[:2000])
-    refused(mtgp.mtgp_plan_set_stats, p3, **PAPER)
+    # a state size without an instantiation of the fused kernel (N = 2696)
+    gb = mtgp.mtgp_params_generate(86243, workloads.PARAM_SEED)
+    sb = mtgp.mtgp_init_statuses(gb, np.arange(2, dtype=np.uint32))
+    pb = mtgp.mtgp_plan_create(sb, [0, 1], [1000, 1000], mtgp.MTGP_U32, out[:2000])
+    refused(mtgp.mtgp_plan_set_stats, pb, **PAPER)
