@@ -46,11 +46,12 @@
 // Until both are settled the piece's rows take the slow path, so the full
 // rows' loop is the same as for unsplit launches.
 //
-// Short states (M < 9, e.g. Mexp 3217: N = 101, N - pos 64 .. 99) take the
-// slow path for every row: it advances one 32-column sub-step at a time,
-// reading each sub-step's words before writing them, which is exact while
-// N - pos >= 32 (a wrapped pick-up of column c then lands on a column below
-// the sub-step, already written).
+// Short states (M < 9, e.g. Mexp 3217: N = 101, N - pos 64 .. 99) advance
+// full rows one 32-column sub-step at a time (fused_rows_short, which reads a
+// sub-step ahead while N - pos >= 64); the slow path reads each sub-step's
+// words before writing them, which is exact while N - pos >= 32 (a wrapped
+// pick-up of column c then lands on a column below the sub-step, already
+// written).
 //
 // Ballots, shuffles and reductions run in warp-uniform control flow.
 #pragma once
@@ -366,6 +367,60 @@ __device__ __forceinline__ void fused_rows(uint32_t (&r)[M], uint32_t* Sw, uint3
     }
 }
 
+// nfull consecutive full rows of one request for short states (M < 9, no
+// 128-word pipelined step fits): one 32-column sub-step at a time, with the
+// statistics of each sub-step's outputs.  The words of the next sub-step are
+// read before this sub-step's words are written, which is exact while
+// N - pos >= 64: none of them is written by this sub-step, and a wrapped
+// pick-up lands on a column of an earlier, already written sub-step.
+template <int M, int FMT>
+__device__ __forceinline__ void fused_rows_short(uint32_t (&r)[M], uint32_t* Sw, uint32_t* ow, const uint32_t* Q,
+                                                 const RowP& P, uint32_t lane, const uint32_t* __restrict__ Tb,
+                                                 uint32_t last_lane, uint32_t nfull, StatsState& st, uint32_t* h,
+                                                 uint32_t* tab, const StatsArgs& A)
+{
+    static_assert(M >= 3, "the look-ahead read of the last sub-step needs three column groups");
+    const uint32_t N = P.n;
+    const uint32_t lower = (1u << lane) - 1u;
+    const bool last_ok = lane <= last_lane;
+    const uint32_t nlast = last_lane + 1u;
+    const uint32_t hs = hist_addr(h);
+    const uint32_t own = own_addr(h, lane, A);
+    uint32_t x1 = Sw[1];
+    uint32_t xp = Q[0];
+    uint32_t xq = Q[-1];
+    for (uint32_t q = 0; q < nfull; ++q, ow += N) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int mn = m + 1 < M ? m + 1 : 0;   // the next sub-step (of the next row after the last)
+            const uint32_t y1 = Sw[32 * mn + 1];
+            const uint32_t yp = Q[32 * mn];
+            const uint32_t yq = Q[32 * mn - 1];
+            const uint32_t yy = (r[m] & P.mask) ^ x1;
+            const uint32_t y = yy ^ (yy << P.sh1) ^ (xp >> P.sh2);
+            const uint32_t xn = y ^ tbl(Tb, 0u, y);
+            const uint32_t o = temper_convert<FMT>(xn, temper_index(xq), Tb);
+            const bool lastg = m + 1 == M;
+            const bool valid = !lastg || last_ok;
+            const uint32_t n = lastg ? nlast : 32u;
+            const uint32_t ad = gap_run(o, valid, 0u, n, lane, lower, st, hs, own, A);
+            ham_run(valid ? __popc(o & A.hmask) : 0u, 0u, n, lane, st, tab, A);
+            if (valid) {
+                r[m] = xn;
+                Sw[32 * m] = xn;
+                if (32u * (uint32_t)m < P.mirror)
+                    Sw[32 * m + N] = xn;
+                __stcs(ow + 32 * m, o);
+            }
+            __syncwarp();
+            count_at(ad);
+            x1 = y1;
+            xp = yp;
+            xq = yq;
+        }
+    }
+}
+
 // A row that crosses into the next request or ends the stream (n_valid
 // columns): each lane finds its request; the statistics take the row's
 // sub-steps in order, one run of same-request lanes at a time.
@@ -474,15 +529,21 @@ __device__ __forceinline__ void fused_item(const KParams& KP, const RowP& P, uin
             const uint32_t nfull = (uint32_t)min((seg_end - row) / N, (uint64_t)0xFFFFFFFFu);
             uint32_t* ow = out + sg.out_off + (row - sg.g_start) + lane;
             stats_switch(st, s, lane, h, tab, segs, A);
-            if (M < 9 || st.lead) {
-                // short states (no 128-word pipelined step fits), or a piece
-                // whose first gap or first pair is still open: one row at a
-                // time on the slow path, one 32-column sub-step after another
+            if (st.lead || (M < 9 && N - P.pos < 64u)) {
+                // a piece whose first gap or first pair is still open: one row
+                // at a time on the slow path, which records them (also short
+                // states too close for the look-ahead read, N - pos < 64)
                 fused_row_slow<M>(r, Sw, Q, P, lane, Tb, N, row, segs, s, s_end, out, st, h, tab, A);
                 row += N;
                 continue;
             }
             if constexpr (M < 9) {
+                if (sg.fmt == 0)
+                    fused_rows_short<M, 0>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+                else if (sg.fmt == 1)
+                    fused_rows_short<M, 1>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
+                else
+                    fused_rows_short<M, 2>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);
             } else if (A.K >= 128u) {
                 if (sg.fmt == 0)
                     fused_rows<M, 0, true>(r, Sw, ow, Q, P, lane, Tb, last_lane, nfull, st, h, tab, A);

@@ -251,6 +251,30 @@ def test_fused_stats_short_states(mexp, split):
     _run(st, op, ids, counts, mtgp.MTGP_U32, **PAPER, split=split)
 
 
+def test_fused_stats_short_states_float_and_short_blocks():
+    """Mexp 3217 in the [0, 1) float format, Hamming blocks of 32 values (one
+    sub-step each) and a rarely visited gap interval."""
+    gp = mtgp.mtgp_params_generate(3217, workloads.PARAM_SEED)
+    op = oracle.params_generate(3217, workloads.PARAM_SEED)
+    rng = np.random.default_rng(3217)
+    ids, counts = _requests(rng, 12, 6, op.n, 90000)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(12, dtype=np.uint32))
+    _run(st, op, ids, counts, mtgp.MTGP_F32_01, (20, 10, 1023), (9, 5, 160, [70, 80, 90]))
+
+
+@pytest.mark.parametrize("gap_words", [40, 33])
+def test_fused_stats_short_states_close_pick_up(gap_words):
+    """A user set at Mexp 3217 with N - pos below 64 (no look-ahead read):
+    every row goes through the sub-step-at-a-time slow path."""
+    o = oracle.params_generate(3217, workloads.PARAM_SEED)
+    op = oracle.params_from_fields(3217, o.n - gap_words, o.sh1, o.sh2, list(o.rec_basis), list(o.tmp_basis))
+    gp = mtgp.mtgp_params_create(3217, op.pos, op.sh1, op.sh2, list(op.rec_tbl), list(op.tmp_tbl))
+    rng = np.random.default_rng(gap_words)
+    ids, counts = _requests(rng, 10, 5, op.n, 60000)
+    st = mtgp.mtgp_init_statuses(gp, np.arange(10, dtype=np.uint32))
+    _run(st, op, ids, counts, mtgp.MTGP_U32, **PAPER)
+
+
 def test_fused_stats_plan_without_work():
     """Requests of zero numbers: no launch runs, and the counts read back are zeros."""
     gp = mtgp.mtgp_params_generate(11213, workloads.PARAM_SEED)
