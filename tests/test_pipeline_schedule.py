@@ -12,6 +12,11 @@ lists standing in for the shared row and per-lane registers, and requires the
 oracle's sequence (Sec. 2 recursion and tempering) for many parameter sets.
 A negative control shows the schedule is wrong for N - pos < 256, i.e. the
 check is sensitive to the ordering argument.
+
+Short states (Mexp 3217, 4253: four or five column groups, no 128-word step
+fits) are counted by the statistics kernel one 32-column sub-step at a time,
+with the loads of the next sub-step issued before the stores of the current
+one: the same schedule with W = 32, exact while N - pos >= 64.
 """
 import numpy as np
 import pytest
@@ -21,11 +26,12 @@ import oracle
 M32 = 0xFFFFFFFF
 
 
-def _emulate(p, state, n_rows):
+def _emulate(p, state, n_rows, K=4, ahead=True):
+    """K: column groups per step (W = 32 K words).  ahead: the next step's
+    loads before the current step's stores; else after them."""
     N, pos = p.n, p.pos
     rec, tmp = list(p.rec_tbl), list(p.tmp_tbl)
     M = (N + 31) // 32                      # 32-column groups
-    K = 4                                   # groups per step (W = 128)
     n_steps = (M + K - 1) // K
     mirror = 32 * ((pos + 31 + 31) // 32)   # mirrored columns after S[N)
     S = [0] * (N + mirror + 4)
@@ -45,7 +51,9 @@ def _emulate(p, state, n_rows):
         row = [None] * N
         for st in range(n_steps):
             s0 = st * K
-            nxt = load_step(s0 + K if st + 1 < n_steps else 0)   # before this step's stores
+            nxt_s0 = s0 + K if st + 1 < n_steps else 0
+            if ahead:
+                nxt = load_step(nxt_s0)             # before this step's stores
             new = {}
             for i, lanes in cur.items():
                 m = s0 + i
@@ -63,7 +71,7 @@ def _emulate(p, state, n_rows):
                     if 32 * m < mirror:
                         S[N + 32 * m + l] = xn
                     row[32 * m + l] = o
-            cur = nxt
+            cur = nxt if ahead else load_step(nxt_s0)
         out.extend(row)
     return np.array(out, np.uint32), np.array(S[:N], np.uint32)
 
@@ -106,3 +114,46 @@ def test_schedule_breaks_below_the_bound(gap):
     ref, _ = oracle.generate(p, state, 3 * p.n)
     got, _ = _emulate(p, state, 3)
     assert not np.array_equal(got, ref)
+
+
+def _short_cases():
+    out = [oracle.params_generate(3217, seed) for seed in (0x5EED, 1, 2)]
+    for mexp in (3217, 4253):
+        n = mexp // 32 + 1
+        out += [_case(mexp, 1), _case(mexp, 2), _case(mexp, n - 64)]
+    return out
+
+
+@pytest.mark.parametrize("p", _short_cases(), ids=lambda p: "mexp%d_n%d_pos%d" % (p.mexp, p.n, p.pos))
+def test_short_state_lookahead_equals_sequential(p):
+    """One 32-column sub-step per step, the next sub-step's loads before the
+    current one's stores (the statistics kernel's short-state row loop)."""
+    assert p.n - p.pos >= 64
+    state = oracle.init_state(p, 4)
+    ref, ref_state = oracle.generate(p, state, 4 * p.n)
+    got, got_row = _emulate(p, state, 4, K=1)
+    np.testing.assert_array_equal(got, ref)
+    np.testing.assert_array_equal(got_row, ref_state)
+
+
+@pytest.mark.parametrize("gap", [63, 40, 33])
+def test_short_state_lookahead_breaks_below_the_bound(gap):
+    """Negative control: with N - pos < 64 a look-ahead pick-up reads a word
+    the current sub-step has not written yet; such sets take the kernel's
+    read-then-write path instead."""
+    p = _case(3217, 3217 // 32 + 1 - gap)
+    state = oracle.init_state(p, 4)
+    ref, _ = oracle.generate(p, state, 4 * p.n)
+    got, _ = _emulate(p, state, 4, K=1)
+    assert not np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("gap,exact", [(32, True), (33, True), (63, True), (31, False), (20, False)])
+def test_short_state_read_then_write_bound(gap, exact):
+    """Sub-steps that load their words after the previous sub-step's stores
+    (the statistics kernel's slow path) are exact while N - pos >= 32."""
+    p = _case(3217, 3217 // 32 + 1 - gap)
+    state = oracle.init_state(p, 4)
+    ref, _ = oracle.generate(p, state, 4 * p.n)
+    got, _ = _emulate(p, state, 4, K=1, ahead=False)
+    assert np.array_equal(got, ref) == exact
