@@ -14,7 +14,9 @@ order and counts the crossing gaps and pairs.  Both are restated here, with
 Python integers for the warp's lanes, and must give the oracle's gap
 histogram (Knuth's gap test on one bit field) and Hamming pair table (the
 weights of consecutive L-bit blocks, classed by the bounds) for arbitrary
-cuts.  A negative control shows the stitch is needed.
+cuts.  Blocks of at least 128 values are also updated per 128-value step, as
+the kernel's full rows do: a step's positions from the block's end on belong
+to the next block.  A negative control shows the stitch is needed.
 """
 import numpy as np
 import pytest
@@ -43,9 +45,11 @@ def _class(w, A):
     return sum(1 for v in A["bounds"] if v <= w)
 
 
-def _piece(x, off, A):
+def _piece(x, off, A, hw=32):
     """Counts of one piece (values x at position off of its request) and its
-    record for the stitch."""
+    record for the stitch.  hw: values per Hamming update, 32 (per sub-step)
+    or 128 (per 128-value step, for blocks of at least 128 values)."""
+    assert hw == 32 or A["K"] >= hw
     K, C, t = A["K"], A["C"], A["t"]
     hist = [0] * (t + 1)
     tab = [0] * (C * C)
@@ -87,13 +91,17 @@ def _piece(x, off, A):
                 g = l - lower - 1 if lower != NONE else l + run
                 hist[min(g, t)] += 1
         run = n - 1 - _hibit(ballot) if ballot else run + n
-        w = [_popc(o[l] & A["hmask"]) if l < n else 0 for l in range(32)]
+    for g0 in range(0, len(x), hw):
+        # a step ends at most one block (hw <= K): its positions >= rem
+        # belong to the next block
+        n = min(hw, len(x) - g0)
+        w = [_popc(int(x[g0 + p]) & A["hmask"]) if p < n else 0 for p in range(hw)]
         if rem > n:
-            acc = [a + v for a, v in zip(acc, w)]
+            acc = [a + sum(w[l::32]) for l, a in enumerate(acc)]
             rem -= n
         else:
-            W = sum(acc[l] + (w[l] if l < rem else 0) for l in range(32))
-            acc = [w[l] if l >= rem else 0 for l in range(32)]
+            W = sum(acc) + sum(w[:rem])
+            acc = [sum(w[p] for p in range(l, hw, 32) if p >= rem) for l in range(32)]
             block_end(W)
             rem += K - n
     part = sum(acc)
@@ -128,14 +136,14 @@ def _stitch(pieces, recs, A, hist, tab):
             wa, wb = r["ta"], r["tb"]
 
 
-def _split_counts(x, cuts, A, stitch=True):
+def _split_counts(x, cuts, A, stitch=True, hw=32):
     edges = [0] + sorted(cuts) + [len(x)]
     pieces = [(edges[i], edges[i + 1] - edges[i]) for i in range(len(edges) - 1)]
     hist = [0] * (A["t"] + 1)
     tab = [0] * (A["C"] ** 2)
     recs = []
     for off, n in pieces:
-        h, tb, rec = _piece(x[off:off + n], off, A)
+        h, tb, rec = _piece(x[off:off + n], off, A, hw)
         hist = [a + v for a, v in zip(hist, h)]
         tab = [a + v for a, v in zip(tab, tb)]
         recs.append(rec)
@@ -166,8 +174,13 @@ def _oracle_counts(x, gap, hamming):
             oracle.hamming_pairs(x, rs, s, L, bounds).ravel())
 
 
-@pytest.mark.parametrize("case", range(len(CASES)))
-def test_random_cuts_equal_whole_request(case):
+# per-128-value-step updates only where a block holds at least 128 values
+WIDTHS = [(c, 32) for c in range(len(CASES))] + \
+         [(c, 128) for c, (_, h) in enumerate(CASES) if h[2] // h[1] >= 128]
+
+
+@pytest.mark.parametrize("case,hw", WIDTHS)
+def test_random_cuts_equal_whole_request(case, hw):
     gap, hamming = CASES[case]
     A = _args(gap, hamming)
     rng = np.random.default_rng(40 + case)
@@ -177,7 +190,7 @@ def test_random_cuts_equal_whole_request(case):
         k = int(rng.integers(0, 8))
         cuts = sorted(set(int(c) for c in rng.integers(1, n, k))) if n > 1 else []
         want_h, want_t = _oracle_counts(x, gap, hamming)
-        h, tb = _split_counts(x, cuts, A)
+        h, tb = _split_counts(x, cuts, A, hw=hw)
         np.testing.assert_array_equal(h, want_h, err_msg="gap, cuts %s" % cuts)
         np.testing.assert_array_equal(tb, want_t, err_msg="Hamming, cuts %s" % cuts)
 
@@ -196,9 +209,10 @@ def test_cuts_at_block_edges_and_pairs_over_many_pieces():
     for cuts in ([K, 2 * K, 4 * K], [K - 1, K + 1, 2 * K - 1, 2 * K + 1],
                  list(range(5, 12 * K, 37)), [3 * K + 1, 4 * K, 5 * K + 3, 6 * K + 100],
                  list(range(1, 70))):
-        h, tb = _split_counts(x, cuts, A)
-        np.testing.assert_array_equal(h, want_h, err_msg="gap, cuts %s" % cuts[:8])
-        np.testing.assert_array_equal(tb, want_t, err_msg="Hamming, cuts %s" % cuts[:8])
+        for hw in (32, 128):
+            h, tb = _split_counts(x, cuts, A, hw=hw)
+            np.testing.assert_array_equal(h, want_h, err_msg="gap, cuts %s" % cuts[:8])
+            np.testing.assert_array_equal(tb, want_t, err_msg="Hamming, %d, cuts %s" % (hw, cuts[:8]))
 
 
 def test_pieces_without_the_stitch_miss_counts():
