@@ -1505,8 +1505,9 @@ static mtgp_status build_split_stats(mtgp_plan* p)
 // CTA, as many resident CTAs per SM as the plan's configuration asks warps
 // per SM (warps_per_cta x ctas_per_sm / 8, at least 1; occupancy maximum when
 // ctas_per_sm is 0), persistent grid.  The kernel takes single-warp items
-// with 128-word pipelined steps, so every parameter set needs N - pos >= 256
-// (the handle's representative set has the largest pos of its sets).
+// with 128-word pipelined steps, so every parameter set needs N - pos >= 256,
+// or N - pos >= 32 for short states (ceil(N/32) < 9); the handle's
+// representative set has the largest pos of its sets.
 static mtgp_status stats_geometry(mtgp_plan* p)
 {
     mtgp_streams* st = p->st;
